@@ -1,0 +1,344 @@
+"""Benchmark: keyframe densification at 1920x960 with 6 source views.
+
+One step = one keyframe through the whole hot path: random initialisation,
+8 red-black iterations of propagation + refinement (11x11 window sampled at
+stride 2, bilateral weights, best-3 of 6 views), then the geometric
+consistency filter of that keyframe against 4 neighbouring depth maps.
+Inputs are seeded synthetic panoramas (scenes/) already resident in HBM;
+the L2 is flushed between timed steps and each step is timed with CUDA
+events on the launching stream.
+
+--impl reference times the CPU oracle on the same workload (bounded sample
+per step: random initialisation plus one half-sweep of the 1920x960 frame,
+scaled to a keyframe).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, H, N_SRC, ITERS = 1920, 960, 6, 8
+N_NEIGHBOURS = 4
+METRIC = "keyframes/s (1920x960, 6 views, 11x11/2 window, 8 iterations, best-3, + consistency filter)"
+WORKLOAD = "equirect PatchMatch densify 1920x960 u8, 6 sources, 11x11 stride 2, 8 iters, best-3, filter vs 4 maps"
+# FP32-pipe instructions of one view-sample by the algorithm's own count:
+# transform 9, two four-quadrant arctangents 2 x 12, hypot 3, scale to pixel
+# coordinates 2, bilinear (floor, fraction, footprint, 3 lerps) 12, centred
+# moments 5  ->  55.
+OPS_PER_VIEW_SAMPLE = 55
+FP32_LANES_PER_SM = 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = str(index)
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", self.index, "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def make_workload(seed_scene=1001):
+    """Trajectory of 7 + 4 frames: keyframe = frame 5, sources = frames 2..4, 6..8,
+    filter neighbours = keyframes 3, 4, 6, 7 (their maps are densified in warm-up)."""
+    import scenes
+    traj = scenes.trajectory(11, seed=2000)
+    scene = scenes.Scene(seed=seed_scene)
+    scene.objects = scenes.place_objects(seed_scene + 77, [c for _, _, c in traj], n=20)
+    frames = []
+    for (R, t, C) in traj:
+        img, rg = scene.render(R, t, W, H, with_range=True)
+        frames.append(scenes.Frame(R, t, C, scenes.quantise_u8(img), rg))
+    params = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=ITERS, best_k=3,
+                  sigma_color=0.2, sigma_space=3.0, n_refine=6, neighbor_table=0, seed=42, keyframe_id=5)
+    return frames, params
+
+
+def problem_of(frames, k):
+    srcs = [frames[j] for j in (k - 3, k - 2, k - 1, k + 1, k + 2, k + 3)]
+    return frames[k], srcs
+
+
+def algorithmic_counts():
+    evals = W * H * (1 + ITERS * (8 + 6))
+    view_samples = evals * N_SRC * 36
+    return evals, view_samples
+
+
+def run_gpu(args):
+    import torch
+    import paper_2211_16266_gb300 as pm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    frames, params = make_workload()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pm.Context(local, stream=stream)
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dimg = {k: to_dev(frames[k].image) for k in range(len(frames))}
+    poses = {k: (frames[k].R, frames[k].t) for k in range(len(frames))}
+
+    def args_for(k):
+        _, srcs = problem_of(frames, k)
+        idx = (k - 3, k - 2, k - 1, k + 1, k + 2, k + 3)
+        return dimg[k], poses[k], [dimg[j] for j in idx], [poses[j] for j in idx]
+
+    KF, NB = 5, (3, 4, 6, 7)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        nb_maps = {k: pm.pmsp_densify(ctx, *args_for(k), dict(params, keyframe_id=k)) for k in NB}
+        out = pm.Maps.empty(W, H, device=dev)
+        filt = torch.empty((H, W), dtype=torch.float32, device=dev)
+        agree = torch.empty((H, W), dtype=torch.int32, device=dev)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    kf_args = args_for(KF)
+
+    def step():
+        pm.pmsp_densify(ctx, *kf_args, params, out=out)
+        pm.pmsp_consistency_filter(ctx, out.depth, poses[KF], [nb_maps[k].depth for k in NB],
+                                   [poses[k] for k in NB], 1.0, 2, out=filt, agree=agree)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+
+    # per-kernel timing of one half-sweep launch set (the dominant kernel)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    times = []
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    smi_id = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (str(uuid) if uuid else local)
+    with ClockSampler(smi_id) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+        stream.synchronize()
+    times = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(times)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+
+    # dominant kernel: time the 16 half-sweeps of one keyframe alone (same stream)
+    sweep_ms = time_sweeps(pm, ctx, stream, kf_args, params, out, flush)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = run_e2e(pm, ctx, stream, frames, KF, NB, nb_maps, params, args)
+
+    evals, vs = algorithmic_counts()
+    clocks = clk.summary() or {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    res = dict(
+        metric=METRIC, value=ws * args.steps / (total_ms / 1e3), unit="keyframes/s", n_gpus=ws,
+        steps=args.steps, warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="u8 images, f32 math", data="synthetic",
+        config=dict(workload=WORKLOAD, width=W, height=H, sources=N_SRC, iterations=ITERS, window="11x11/2",
+                    best_k=3, filter_neighbours=N_NEIGHBOURS, l2="flushed (256 MiB write) between steps",
+                    parallelism="replicas" if ws > 1 else "single"),
+        latency_ms=dict(p50=float(np.percentile(times, 50)), p99=float(np.percentile(times, 99))),
+        hypothesis_evals_per_s=ws * evals * args.steps / (total_ms / 1e3),
+        gpu_launches=args.steps * (2 + 2 * ITERS + 1),
+        clocks=clocks,
+    )
+    if rank == 0:
+        peak_mhz = clocks.get("sm_max_mhz") or 2070.0
+        peak = sms * FP32_LANES_PER_SM * peak_mhz * 1e6 / OPS_PER_VIEW_SAMPLE
+        vs_per_sweep = W * H / 2 * 14 * N_SRC * 36
+        achieved = vs_per_sweep / (sweep_ms / 1e3)
+        res["roofline"] = dict(bound="alu", achieved=achieved, peak=peak, unit="view-samples/s",
+                               frac=achieved / peak, traffic=None,
+                               kernel="pixel_kernel<6, SWEEP> (one half-sweep)",
+                               ms_per_launch=sweep_ms,
+                               peak_basis=f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {peak_mhz:.0f} MHz / "
+                                          f"{OPS_PER_VIEW_SAMPLE} ops per view-sample")
+        res["e2e"] = e2e
+        if not args.no_cpu_baseline and ws == 1:
+            res["cpu_baseline"] = cpu_baseline(frames, KF, params)
+        print(json.dumps(res))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def time_sweeps(pm, ctx, stream, kf_args, params, out, flush):
+    """Mean duration of one half-sweep launch (dominant kernel), CUDA events on its stream."""
+    import torch
+    state = pm.Maps(out.depth.clone(), out.normal.clone(), out.cost.clone())
+    reps = 6
+    durs = []
+    with torch.cuda.stream(stream):
+        for r in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pm.pmsp_halfsweep(ctx, *kf_args, params, r & 1, 9 + r // 2, state)
+            b.record(stream)
+            durs.append((a, b))
+    stream.synchronize()
+    # the half-sweep call also uploads 6 textures (device copies); subtract nothing: they are ~10 us
+    return float(np.mean([a.elapsed_time(b) for a, b in durs]))
+
+
+def run_e2e(pm, ctx, stream, frames, KF, NB, nb_maps, params, args):
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    idx = (KF - 3, KF - 2, KF - 1, KF + 1, KF + 2, KF + 3)
+    ref = pin(frames[KF].image)
+    srcs = [pin(frames[j].image) for j in idx]
+    nbd = [pin(nb_maps[k].depth.cpu().numpy()) for k in NB]
+    out = pm.Maps(pin(np.zeros((H, W), np.float32)), pin(np.zeros((3, H, W), np.float32)),
+                  pin(np.zeros((H, W), np.float32)))
+    filt = pin(np.zeros((H, W), np.float32))
+    agree = pin(np.zeros((H, W), np.int32))
+    poses = lambda ks: [(frames[k].R, frames[k].t) for k in ks]
+
+    def step():
+        pm.pmsp_densify(ctx, ref, (frames[KF].R, frames[KF].t), srcs, poses(idx), params, out=out)
+        pm.pmsp_consistency_filter(ctx, out.depth, (frames[KF].R, frames[KF].t), nbd, poses(NB), 1.0, 2,
+                                   out=filt, agree=agree)
+
+    for _ in range(min(args.warmup, 2)):
+        step()
+    n = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        step()
+    dt = (time.perf_counter() - t0) / n
+    h2d = ref.nbytes + sum(s.nbytes for s in srcs) + out.depth.nbytes + sum(d.nbytes for d in nbd)
+    d2h = out.depth.nbytes + out.normal.nbytes + out.cost.nbytes + filt.nbytes + agree.nbytes
+    return dict(value=1.0 / dt, unit="keyframes/s", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
+                steps=n, timer="host wall clock around the C-ABI calls")
+
+
+def cpu_baseline(frames, KF, params):
+    """The oracle on the host cores: random init + one half-sweep of the keyframe,
+    scaled to a keyframe (init + 2 x iterations half-sweeps)."""
+    import oracle
+    ref, srcs = problem_of(frames, KF)
+    pb = oracle.Problem(ref.image, (ref.R, ref.t), [f.image for f in srcs], [(f.R, f.t) for f in srcs], **params)
+    t0 = time.perf_counter()
+    d, n, c = pb.init()
+    t1 = time.perf_counter()
+    pb.halfsweep(d, n, c, 0, 0)
+    t2 = time.perf_counter()
+    t_kf = (t1 - t0) + 2 * ITERS * (t2 - t1)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return dict(value=1.0 / t_kf, unit="keyframes/s", cores=int(os.environ.get("OMP_NUM_THREADS", cores)),
+                kind="oracle", sample=f"FP64 oracle: random init ({t1 - t0:.1f} s) + one red half-sweep "
+                                      f"({t2 - t1:.1f} s) of the 1920x960 keyframe, scaled to init + "
+                                      f"{2 * ITERS} half-sweeps; filter not included")
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    frames, params = make_workload()
+    KF = 5
+    per = []
+    for _ in range(args.steps):
+        cb = cpu_baseline(frames, KF, params)
+        per.append(1.0 / cb["value"])
+    val = args.steps / sum(per)
+    cb["value"] = val
+    print(json.dumps(dict(impl="reference", metric=METRIC, value=val, unit="keyframes/s", n_gpus=ws,
+                          steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * sum(per) / args.steps,
+                          higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                          data="synthetic", config=dict(workload=WORKLOAD), cpu_baseline=cb,
+                          e2e=dict(value=val, unit="keyframes/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

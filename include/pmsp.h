@@ -1,0 +1,201 @@
+/*
+ * pmsp.h - C ABI of the GB300 PatchMatch-Stereo-Panorama densification library.
+ *
+ * The library computes, for one reference equirectangular keyframe and a small
+ * neighbourhood of source keyframes with known poses, a per-pixel plane
+ * hypothesis (range along the pixel ray + unit normal) by PatchMatch stereo:
+ * random initialisation (paper Sec. III-B), red-black propagation over an
+ * 8-neighbourhood (Sec. III-C, Fig. 5), six shrinking random refinement tests
+ * (Sec. III-C, item 1), scored by a bilaterally weighted NCC of the reference
+ * patch against its reprojection through the plane into every source
+ * panorama, averaged over the best k views; and a multi-view geometric
+ * consistency filter over neighbouring depth maps (Sec. III).
+ *
+ * Conventions (all calls):
+ *  - Panorama W x H, row-major, W even. Pixel (u, v) looks along longitude
+ *    2*pi*(u+0.5)/W - pi and latitude pi/2 - pi*(v+0.5)/H; camera frame x right,
+ *    y down, z forward.
+ *  - Poses are world->camera, X_c = R X_w + t, R row-major, in double.
+ *  - "Depth" is the range along the pixel ray, metres. Normals are unit vectors
+ *    in the reference camera frame, stored as three planes nx, ny, nz of W*H
+ *    floats each (normal[0..N), normal[N..2N), normal[2N..3N)).
+ *  - uint8 images are intensities DN/255; fp16/fp32 images are taken as given
+ *    and are expected to lie in [0, 1].
+ *  - Ownership: the caller owns every buffer passed in and out; the library
+ *    never frees or retains caller memory beyond a call. The context owns its
+ *    internal buffers (texture arrays, staging, error flag) and frees them in
+ *    pmsp_destroy.
+ *  - Errors: every call returns PMSP_OK (0) or a negative code below; the
+ *    text of the last failure is available from pmsp_last_error. Nothing is
+ *    thrown and nothing aborts across the ABI.
+ *  - Streams: work is enqueued on the context's stream. A call whose inputs
+ *    and outputs are all device memory returns once the work is enqueued
+ *    (asynchronous); a call touching host memory returns after the results
+ *    are back on the host. pmsp_sync waits for the stream and reports any
+ *    error the kernels flagged.
+ *  - Threads: a context is used by one host thread at a time, except the
+ *    serving calls (submit/poll/wait), which are internally locked.
+ */
+#ifndef PMSP_H
+#define PMSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMSP_ABI_VERSION 1
+#define PMSP_MAX_SOURCES 16
+#define PMSP_MAX_PATCH_W 21
+
+/* Status codes. */
+#define PMSP_OK 0
+#define PMSP_EINVAL (-1)    /* invalid argument or size */
+#define PMSP_ENOMEM (-2)    /* device or host allocation failed */
+#define PMSP_EADMIT (-3)    /* request exceeds the context's memory cap */
+#define PMSP_EBUSY (-4)     /* no free slot, try again later */
+#define PMSP_ETIMEDOUT (-5) /* bounded wait expired */
+#define PMSP_ECUDA (-6)     /* CUDA runtime error (text in pmsp_last_error) */
+#define PMSP_EDEVICE (-7)   /* a kernel flagged an error (bounds/consistency) */
+#define PMSP_ENOTFOUND (-8) /* unknown frame id or ticket */
+
+typedef enum { PMSP_U8 = 0, PMSP_F16 = 1, PMSP_F32 = 2 } pmsp_format;
+typedef enum { PMSP_HOST = 0, PMSP_DEVICE = 1 } pmsp_memory;
+
+/* A grayscale panorama. pitch_bytes >= w * element size; data is host or
+ * device memory according to `memory`. */
+typedef struct {
+    int32_t w, h;
+    int64_t pitch_bytes;
+    int32_t format; /* pmsp_format */
+    int32_t memory; /* pmsp_memory */
+    const void* data;
+} pmsp_image;
+
+/* World->camera pose, X_c = R X_w + t (R row-major). */
+typedef struct {
+    double R[9];
+    double t[3];
+} pmsp_pose;
+
+/* PatchMatch parameters (see pmsp_default_params for the defaults). */
+typedef struct {
+    float d_min, d_max;       /* range bounds in metres, 0 < d_min < d_max */
+    int32_t patch_w;          /* window extent in pixels, odd, <= PMSP_MAX_PATCH_W */
+    int32_t patch_stride;     /* sampling step inside the window, >= 1 */
+    int32_t iterations;       /* red-black iterations */
+    int32_t best_k;           /* views averaged per cost, 1 <= best_k <= n_src */
+    float sigma_color;        /* bilateral colour sigma (normalised units); <= 0: off */
+    float sigma_space;        /* bilateral spatial sigma (pixels); <= 0: off */
+    int32_t n_refine;         /* random refinement tests per half-sweep (paper: 6) */
+    int32_t neighbor_table;   /* 0: axis distances {3, 5}; 1: {1, 5} */
+    uint64_t seed;            /* Philox key word 0 */
+    uint64_t keyframe_id;     /* Philox key word 1 */
+} pmsp_params;
+
+/* Plane map: range, normal (3 planes) and cost, each w*h floats, host or
+ * device memory according to `memory`. Any of the pointers may be NULL where
+ * a call says so. */
+typedef struct {
+    int32_t w, h;
+    int32_t memory; /* pmsp_memory */
+    float* depth;
+    float* normal;
+    float* cost;
+} pmsp_maps;
+
+typedef struct {
+    int32_t device;          /* CUDA device ordinal */
+    void* stream;            /* cudaStream_t to enqueue on (cudaStreamLegacy, 0x1, for the
+                                legacy default stream); NULL: the context creates one */
+    uint64_t mem_cap_bytes;  /* serving admission cap (0: 40 GiB) */
+    int32_t ring_capacity;   /* frames kept in the device ring (0: 64) */
+    int32_t max_active;      /* serving slots (0: 32) */
+} pmsp_ctx_opts;
+
+typedef struct pmsp_ctx pmsp_ctx;
+
+/* Create a context on opts->device (NULL opts: device 0, own stream). */
+int pmsp_create(pmsp_ctx** out, const pmsp_ctx_opts* opts);
+/* Wait for outstanding work and free everything the context owns. NULL is a no-op. */
+int pmsp_destroy(pmsp_ctx* ctx);
+/* Text of the most recent failure on this context ("" if none). Valid until the next call. */
+const char* pmsp_last_error(pmsp_ctx* ctx);
+/* Block until the context stream is idle; PMSP_EDEVICE if a kernel flagged an error. */
+int pmsp_sync(pmsp_ctx* ctx);
+/* Fill *p with the defaults: d 0.3..10 m, 11x11 window at stride 2, 8
+ * iterations, best_k 3, sigma_color 0.2, sigma_space 3 px, 6 refinement
+ * tests, table 0, seed 42, keyframe 0. */
+void pmsp_default_params(pmsp_params* p);
+
+/*
+ * Densify one keyframe (Sec. III-B initialisation, then `iterations` x red and
+ * black half-sweeps of Sec. III-C propagation and refinement).
+ *   ref, ref_pose        reference panorama and pose
+ *   srcs, src_poses      n_src source panoramas (1 <= n_src <= PMSP_MAX_SOURCES),
+ *                        any size each, and their poses
+ *   p                    parameters
+ *   out                  w x h of the reference; depth, normal, cost all required.
+ * Returns PMSP_EINVAL for odd w, best_k outside [1, n_src], a bad window, a bad
+ * range, a NULL pointer or an unknown format.
+ */
+int pmsp_densify(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pose,
+                 const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
+                 const pmsp_params* p, pmsp_maps* out);
+
+/*
+ * Matching cost (Sec. III-C: rectangular patch in the reference, its
+ * reprojection through the plane into every source) of the given planes:
+ * planes->depth and planes->normal are read, planes->cost is written.
+ */
+int pmsp_cost_map(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pose,
+                  const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
+                  const pmsp_params* p, pmsp_maps* planes);
+
+/* Random initialisation (Sec. III-B) plus initial cost into out. */
+int pmsp_init(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pose,
+              const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
+              const pmsp_params* p, pmsp_maps* out);
+
+/*
+ * One half-sweep (Sec. III-C) in place on `state`: every pixel with
+ * (u + v) % 2 == colour tries its 8 neighbours' planes and p->n_refine random
+ * refinements (Philox counter iteration word = `iteration`), keeping a
+ * candidate only if its cost is strictly lower.
+ */
+int pmsp_halfsweep(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pose,
+                   const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
+                   const pmsp_params* p, int colour, int iteration, pmsp_maps* state);
+
+/*
+ * Geometric consistency filter (Sec. III): a reference pixel keeps its range
+ * if, in at least min_views of the n neighbour depth maps, lifting it to 3-D,
+ * reading the neighbour's range at the nearest pixel and reprojecting that
+ * point lands within max_reproj_px pixels of where it started; otherwise its
+ * range becomes 0.
+ *   ref        reference depth (ref->depth read)
+ *   nbrs       n neighbour maps (depth read; any size each), 1 <= n <= PMSP_MAX_SOURCES
+ *   inout      depth written (may alias ref->depth)
+ *   agree      optional (NULL) w*h int32 receiving the number of agreeing views,
+ *              same memory kind as inout
+ */
+int pmsp_consistency_filter(pmsp_ctx* ctx, const pmsp_maps* ref, const pmsp_pose* ref_pose,
+                            const pmsp_maps* nbrs, const pmsp_pose* nbr_poses, int n,
+                            float max_reproj_px, int min_views, pmsp_maps* inout,
+                            int32_t* agree);
+
+/*
+ * Bilinear sample of img at n continuous pixel coordinates (integers are pixel
+ * centres; longitude wrapped, latitude clamped), the source fetch the cost uses.
+ * uc, vc, out: n floats each, in the memory kind of img.
+ */
+int pmsp_sample_bilinear(pmsp_ctx* ctx, const pmsp_image* img, int n, const float* uc,
+                         const float* vc, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMSP_H */

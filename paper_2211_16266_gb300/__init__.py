@@ -1,0 +1,358 @@
+"""Python binding of the GB300 PatchMatch-Stereo-Panorama densification library.
+
+Argument marshalling only: every step of the densification runs in the CUDA
+kernels of libpmsp.so behind the C ABI declared in include/pmsp.h. The
+functions carry the C names (pmsp_create, pmsp_densify, ...). Arrays may be
+numpy arrays (host memory) or torch tensors (device memory when on CUDA);
+torch supplies device memory and streams only.
+
+Importing this module fails loudly when libpmsp.so has not been built
+(`python -c "import __graft_entry__ as g; g.build()"`); there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpmsp.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libpmsp.so is missing at {LIB_PATH}: build the CUDA library first "
+                      "(paper_2211_16266_gb300/_build.py); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PMSP_OK = 0
+PMSP_EINVAL = -1
+PMSP_ENOMEM = -2
+PMSP_EADMIT = -3
+PMSP_EBUSY = -4
+PMSP_ETIMEDOUT = -5
+PMSP_ECUDA = -6
+PMSP_EDEVICE = -7
+PMSP_ENOTFOUND = -8
+PMSP_U8, PMSP_F16, PMSP_F32 = 0, 1, 2
+PMSP_HOST, PMSP_DEVICE = 0, 1
+MAX_SOURCES = 16
+
+_ERR_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EADMIT", -4: "EBUSY", -5: "ETIMEDOUT",
+              -6: "ECUDA", -7: "EDEVICE", -8: "ENOTFOUND"}
+
+
+class PmspError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pmsp_image(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("pitch_bytes", ctypes.c_int64),
+                ("format", ctypes.c_int32), ("memory", ctypes.c_int32), ("data", ctypes.c_void_p)]
+
+
+class pmsp_pose(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+class pmsp_params(ctypes.Structure):
+    _fields_ = [("d_min", ctypes.c_float), ("d_max", ctypes.c_float), ("patch_w", ctypes.c_int32),
+                ("patch_stride", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("best_k", ctypes.c_int32), ("sigma_color", ctypes.c_float),
+                ("sigma_space", ctypes.c_float), ("n_refine", ctypes.c_int32),
+                ("neighbor_table", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("keyframe_id", ctypes.c_uint64)]
+
+
+class pmsp_maps(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("memory", ctypes.c_int32),
+                ("depth", ctypes.c_void_p), ("normal", ctypes.c_void_p), ("cost", ctypes.c_void_p)]
+
+
+class pmsp_ctx_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("mem_cap_bytes", ctypes.c_uint64),
+                ("ring_capacity", ctypes.c_int32), ("max_active", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.POINTER(pmsp_image)
+_O = ctypes.POINTER(pmsp_pose)
+_R = ctypes.POINTER(pmsp_params)
+_M = ctypes.POINTER(pmsp_maps)
+_F = ctypes.c_void_p
+
+_SIGS = {
+    "pmsp_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(pmsp_ctx_opts)], ctypes.c_int),
+    "pmsp_destroy": ([_P], ctypes.c_int),
+    "pmsp_last_error": ([_P], ctypes.c_char_p),
+    "pmsp_sync": ([_P], ctypes.c_int),
+    "pmsp_default_params": ([_R], None),
+    "pmsp_densify": ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M], ctypes.c_int),
+    "pmsp_cost_map": ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M], ctypes.c_int),
+    "pmsp_init": ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M], ctypes.c_int),
+    "pmsp_halfsweep": ([_P, _I, _O, _I, _O, ctypes.c_int, _R, ctypes.c_int, ctypes.c_int, _M], ctypes.c_int),
+    "pmsp_consistency_filter": ([_P, _M, _O, _M, _O, ctypes.c_int, ctypes.c_float, ctypes.c_int, _M, _F],
+                                ctypes.c_int),
+    "pmsp_sample_bilinear": ([_P, _I, ctypes.c_int, _F, _F, _F], ctypes.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+C_SYMBOLS = tuple(_SIGS)
+
+
+# --------------------------------------------------------------- marshalling
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _format_of(dtype_name):
+    return {"uint8": PMSP_U8, "float16": PMSP_F16, "float32": PMSP_F32}[dtype_name]
+
+
+def make_image(arr, keep):
+    """pmsp_image over a (H, W) numpy array or torch tensor (rows contiguous)."""
+    if _is_torch(arr):
+        if arr.dim() != 2 or arr.stride(1) != 1:
+            raise ValueError("image must be a 2-D tensor with contiguous rows")
+        fmt = _format_of(str(arr.dtype).replace("torch.", ""))
+        im = pmsp_image(arr.shape[1], arr.shape[0], arr.stride(0) * arr.element_size(), fmt,
+                        PMSP_DEVICE if arr.is_cuda else PMSP_HOST, arr.data_ptr())
+    else:
+        a = np.asarray(arr)
+        if a.ndim != 2 or a.strides[1] != a.itemsize:
+            a = np.ascontiguousarray(a)
+        fmt = _format_of(a.dtype.name)
+        im = pmsp_image(a.shape[1], a.shape[0], a.strides[0], fmt, PMSP_HOST, a.ctypes.data)
+        arr = a
+    keep.append(arr)
+    return im
+
+
+def make_pose(pose):
+    R, t = pose
+    p = pmsp_pose()
+    R = np.asarray(R, dtype=np.float64).reshape(9)
+    t = np.asarray(t, dtype=np.float64).reshape(3)
+    for i in range(9):
+        p.R[i] = float(R[i])
+    for i in range(3):
+        p.t[i] = float(t[i])
+    return p
+
+
+def pmsp_default_params(**override):
+    p = pmsp_params()
+    _lib.pmsp_default_params(ctypes.byref(p))
+    for k, v in override.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def make_params(params):
+    if isinstance(params, pmsp_params):
+        return params
+    return pmsp_default_params(**(params or {}))
+
+
+class Maps:
+    """Depth (H, W), normal (3, H, W) and cost (H, W) float32 buffers."""
+
+    def __init__(self, depth, normal, cost):
+        self.depth, self.normal, self.cost = depth, normal, cost
+
+    @classmethod
+    def empty(cls, W, H, device=None):
+        if device is not None:
+            import torch
+            kw = dict(dtype=torch.float32, device=device)
+            return cls(torch.empty((H, W), **kw), torch.empty((3, H, W), **kw), torch.empty((H, W), **kw))
+        return cls(np.zeros((H, W), np.float32), np.zeros((3, H, W), np.float32), np.zeros((H, W), np.float32))
+
+    def c(self):
+        d = self.depth
+        if _is_torch(d):
+            for a in (self.depth, self.normal, self.cost):
+                if a is not None:
+                    assert a.is_contiguous() and str(a.dtype) == "torch.float32"
+            mem = PMSP_DEVICE if d.is_cuda else PMSP_HOST
+            ptr = lambda a: a.data_ptr() if a is not None else None
+            H, W = d.shape
+        else:
+            for a in (self.depth, self.normal, self.cost):
+                if a is not None:
+                    assert a.dtype == np.float32 and a.flags.c_contiguous
+            mem = PMSP_HOST
+            ptr = lambda a: a.ctypes.data if a is not None else None
+            H, W = d.shape
+        return pmsp_maps(W, H, mem, ptr(self.depth), ptr(self.normal), ptr(self.cost))
+
+    def numpy(self):
+        f = (lambda a: a.detach().cpu().numpy()) if _is_torch(self.depth) else (lambda a: a)
+        return f(self.depth), f(self.normal), f(self.cost)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.data_ptr() if _is_torch(a) else a.ctypes.data
+
+
+class Context:
+    """Owns a pmsp_ctx. stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+
+    def __init__(self, device=0, stream=None, mem_cap_bytes=0, ring_capacity=0, max_active=0):
+        raw = None
+        if stream is not None:
+            raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            if raw == 0:
+                raw = 1  # torch's default stream is the legacy stream (cudaStreamLegacy)
+        opts = pmsp_ctx_opts(device, raw, mem_cap_bytes, ring_capacity, max_active)
+        h = ctypes.c_void_p()
+        rc = _lib.pmsp_create(ctypes.byref(h), ctypes.byref(opts))
+        if rc != PMSP_OK:
+            raise PmspError(rc, "pmsp_create failed")
+        self.h = h
+
+    def check(self, rc):
+        if rc != PMSP_OK:
+            raise PmspError(rc, _lib.pmsp_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if self.h:
+            _lib.pmsp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def pmsp_create(device=0, stream=None, **kw):
+    return Context(device, stream, **kw)
+
+
+def pmsp_destroy(ctx):
+    ctx.close()
+
+
+def pmsp_last_error(ctx):
+    return _lib.pmsp_last_error(ctx.h).decode()
+
+
+def pmsp_sync(ctx):
+    return ctx.check(_lib.pmsp_sync(ctx.h))
+
+
+def _problem(ref, ref_pose, srcs, src_poses, params, keep):
+    n = len(srcs)
+    if n < 1 or n > MAX_SOURCES or len(src_poses) != n:
+        raise ValueError("need 1..16 sources with one pose each")
+    cref = make_image(ref, keep)
+    csrc = (pmsp_image * n)(*[make_image(s, keep) for s in srcs])
+    cpose = (pmsp_pose * n)(*[make_pose(p) for p in src_poses])
+    keep += [csrc, cpose]
+    return cref, make_pose(ref_pose), csrc, cpose, n, make_params(params)
+
+
+def _out_maps(ref, out):
+    if out is not None:
+        return out
+    H, W = ref.shape
+    return Maps.empty(W, H, device=ref.device if _is_torch(ref) and ref.is_cuda else None)
+
+
+def pmsp_densify(ctx, ref, ref_pose, srcs, src_poses, params=None, out=None):
+    """Densify one keyframe; returns Maps (device tensors for device input)."""
+    keep = []
+    cref, rp, cs, cp, n, p = _problem(ref, ref_pose, srcs, src_poses, params, keep)
+    out = _out_maps(ref, out)
+    m = out.c()
+    ctx.check(_lib.pmsp_densify(ctx.h, ctypes.byref(cref), ctypes.byref(rp), cs, cp, n, ctypes.byref(p),
+                                ctypes.byref(m)))
+    return out
+
+
+def pmsp_cost_map(ctx, ref, ref_pose, srcs, src_poses, params, planes):
+    keep = []
+    cref, rp, cs, cp, n, p = _problem(ref, ref_pose, srcs, src_poses, params, keep)
+    m = planes.c()
+    ctx.check(_lib.pmsp_cost_map(ctx.h, ctypes.byref(cref), ctypes.byref(rp), cs, cp, n, ctypes.byref(p),
+                                 ctypes.byref(m)))
+    return planes
+
+
+def pmsp_init(ctx, ref, ref_pose, srcs, src_poses, params=None, out=None):
+    keep = []
+    cref, rp, cs, cp, n, p = _problem(ref, ref_pose, srcs, src_poses, params, keep)
+    out = _out_maps(ref, out)
+    m = out.c()
+    ctx.check(_lib.pmsp_init(ctx.h, ctypes.byref(cref), ctypes.byref(rp), cs, cp, n, ctypes.byref(p),
+                             ctypes.byref(m)))
+    return out
+
+
+def pmsp_halfsweep(ctx, ref, ref_pose, srcs, src_poses, params, colour, iteration, state):
+    keep = []
+    cref, rp, cs, cp, n, p = _problem(ref, ref_pose, srcs, src_poses, params, keep)
+    m = state.c()
+    ctx.check(_lib.pmsp_halfsweep(ctx.h, ctypes.byref(cref), ctypes.byref(rp), cs, cp, n, ctypes.byref(p),
+                                  int(colour), int(iteration), ctypes.byref(m)))
+    return state
+
+
+def pmsp_consistency_filter(ctx, depth, pose, nbr_depths, nbr_poses, max_px=1.0, min_views=2, out=None,
+                            agree=None):
+    """Filter `depth` (H, W) against neighbour depth maps; returns (depth_out, agree)."""
+    n = len(nbr_depths)
+    if _is_torch(depth):
+        import torch
+        out = torch.empty_like(depth) if out is None else out
+        if agree is None:
+            agree = torch.empty(depth.shape, dtype=torch.int32, device=depth.device)
+    else:
+        depth = np.ascontiguousarray(depth, dtype=np.float32)
+        nbr_depths = [np.ascontiguousarray(d, dtype=np.float32) for d in nbr_depths]
+        out = np.zeros_like(depth) if out is None else out
+        if agree is None:
+            agree = np.zeros(depth.shape, np.int32)
+    H, W = depth.shape
+    mem = PMSP_DEVICE if _is_torch(depth) and depth.is_cuda else PMSP_HOST
+    ref = pmsp_maps(W, H, mem, _ptr(depth), None, None)
+    nb = (pmsp_maps * n)(*[pmsp_maps(d.shape[1], d.shape[0], mem, _ptr(d), None, None) for d in nbr_depths])
+    poses = (pmsp_pose * n)(*[make_pose(p) for p in nbr_poses])
+    o = pmsp_maps(W, H, mem, _ptr(out), None, None)
+    ctx.check(_lib.pmsp_consistency_filter(ctx.h, ctypes.byref(ref), ctypes.byref(make_pose(pose)), nb, poses,
+                                           n, float(max_px), int(min_views), ctypes.byref(o), _ptr(agree)))
+    return out, agree
+
+
+def pmsp_sample_bilinear(ctx, img, uc, vc):
+    keep = []
+    im = make_image(img, keep)
+    if _is_torch(img):
+        import torch
+        out = torch.empty_like(uc)
+    else:
+        uc = np.ascontiguousarray(uc, dtype=np.float32)
+        vc = np.ascontiguousarray(vc, dtype=np.float32)
+        out = np.zeros_like(uc)
+    ctx.check(_lib.pmsp_sample_bilinear(ctx.h, ctypes.byref(im), int(uc.shape[0]), _ptr(uc), _ptr(vc), _ptr(out)))
+    return out

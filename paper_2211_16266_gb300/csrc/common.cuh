@@ -1,0 +1,84 @@
+// Shared device-side declarations of the densification kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pmsp.h"
+
+namespace pmsp {
+
+// Tile of reference pixels handled by one block: TILE_W x TILE_H pixels, of
+// which one colour (half of them) is active in a half-sweep; one thread per
+// active pixel.
+constexpr int TILE_W = 32;
+constexpr int TILE_H = 8;
+constexpr int BLOCK_THREADS = (TILE_W / 2) * TILE_H;
+constexpr int MAX_HALO = (PMSP_MAX_PATCH_W - 1) / 2;
+
+// Error bits written to the device error word.
+constexpr unsigned ERR_BAD_INDEX = 1u;
+
+// One source view as the kernels see it.
+struct SourceView {
+    cudaTextureObject_t tex;  // gather-capable texture: x wraps, y clamps, normalised coords
+    float R[9];               // reference camera -> source camera rotation, row-major
+    float t[3];
+    float su, ou;             // u_c = lon * su + ou
+    float sv, ov;             // v_c = lat * sv + ov
+    float inv_w, inv_h;       // 1/W, 1/H of this source
+};
+
+enum Mode : int { MODE_COST = 0, MODE_INIT = 1, MODE_SWEEP = 2 };
+
+struct PixelParams {
+    SourceView src[PMSP_MAX_SOURCES];
+    const uint8_t* ref;   // reference image, linear, row pitch ref_pitch bytes
+    int64_t ref_pitch;
+    int ref_format;       // pmsp_format
+    int W, H;
+    float* depth;         // state planes, W*H each
+    float* nx;
+    float* ny;
+    float* nz;
+    float* cost;
+    float d_min, d_max;
+    float inv_dmin, inv_dmax;
+    int S;                // number of sources
+    int K;                // samples per window axis
+    int stride;           // sample step (pixels)
+    int radius;           // (patch_w - 1) / 2
+    int best_k;
+    int n_refine;
+    int table;            // neighbour table id
+    float wc;             // -log2(e) / (2 sigma_c^2), 0 when off
+    float ws;             // -log2(e) / (2 sigma_s^2), 0 when off
+    unsigned long long seed, keyframe;
+    int colour;
+    int iter;
+    unsigned* err;
+};
+
+struct FilterView {
+    const float* depth;  // neighbour range map, W x H
+    int W, H;
+    float Rf[9], tf[3];  // reference -> neighbour
+    float Rb[9], tb[3];  // neighbour -> reference
+};
+
+struct FilterParams {
+    FilterView nb[PMSP_MAX_SOURCES];
+    const float* depth_in;
+    float* depth_out;
+    int32_t* agree;
+    int W, H, n, min_views;
+    float max_px;
+};
+
+// Launchers (one translation unit per source-count bucket).
+cudaError_t launch_pixel_kernel(const PixelParams& p, int mode, cudaStream_t stream);
+cudaError_t launch_filter_kernel(const FilterParams& p, cudaStream_t stream);
+cudaError_t launch_sample_kernel(cudaTextureObject_t tex, int W, int H, int n, const float* uc,
+                                 const float* vc, float* out, cudaStream_t stream);
+
+}  // namespace pmsp

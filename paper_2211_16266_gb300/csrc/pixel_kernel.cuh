@@ -1,0 +1,345 @@
+// Per-pixel PatchMatch kernels: matching cost, random initialisation and the
+// red-black half-sweep (propagation + refinement), templated on the number
+// of source views the block keeps in registers.
+//
+// Paper: random initialisation of the plane map (Sec. III-B); parallel
+// red-black propagation over an 8-neighbourhood whose inner neighbours sit
+// one position further out than in Galliani et al. (Sec. III-C, Fig. 5);
+// six random refinement tests on a shrinking range (Sec. III-C, item 1). The
+// cost is the bilaterally weighted NCC of the reference patch against its
+// reprojection through the plane into every source, averaged over the best k
+// views (the cost of the PatchMatch works the paper cites).
+//
+// Design: one thread per active pixel of a 32x8 tile (one colour per launch).
+// The reference tile with its halo and the per-row / per-column bearing terms
+// are staged in shared memory; the sample loop runs over the patch with all
+// views innermost, so the plane intersection and the bilateral weight of a
+// sample are shared by every view. Per view four FP32 sums are kept: the
+// source intensity is centred on its value at the first (centre-most)
+// sample, which keeps the variance term free of cancellation.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "camera.cuh"
+#include "common.cuh"
+#include "philox.cuh"
+
+namespace pmsp {
+
+static __constant__ int c_neighbors[2][8][2] = {
+    {{0, -3}, {0, 3}, {-3, 0}, {3, 0}, {0, -5}, {0, 5}, {-5, 0}, {5, 0}},
+    {{0, -1}, {0, 1}, {-1, 0}, {1, 0}, {0, -5}, {0, 5}, {-5, 0}, {5, 0}}};
+
+constexpr int TILE_PITCH = TILE_W + 2 * MAX_HALO;
+constexpr int TILE_ROWS = TILE_H + 2 * MAX_HALO;
+
+struct TileSmem {
+    float ref[TILE_ROWS * TILE_PITCH];  // normalised intensities, halo included
+    float row_cos[TILE_ROWS], row_sin[TILE_ROWS];    // cos lat, sin lat
+    float col_sin[TILE_PITCH], col_cos[TILE_PITCH];  // sin lon, cos lon
+};
+
+// Reference-side constants of one pixel (independent of the hypothesis).
+struct RefStats {
+    float Ip;    // centre intensity
+    float mu;    // weighted mean of the samples
+    float Sw;    // sum of weights
+    float SIc;   // sum w (I - mu)   (zero up to rounding)
+    float varI;  // Sw * sum w (I - mu)^2 - SIc^2
+};
+
+__device__ __forceinline__ float load_ref(const PixelParams& P, int x, int y) {
+    const uint8_t* row = P.ref + (int64_t)y * P.ref_pitch;
+    if (P.ref_format == PMSP_U8) return (float)row[x] * (1.0f / 255.0f);
+    if (P.ref_format == PMSP_F16) return __half2float(reinterpret_cast<const __half*>(row)[x]);
+    return reinterpret_cast<const float*>(row)[x];
+}
+
+__device__ __forceinline__ void stage_tile(const PixelParams& P, TileSmem& sm, int bx, int by) {
+    const int R = P.radius;
+    const int rows = TILE_H + 2 * R, cols = TILE_W + 2 * R;
+    for (int i = threadIdx.x; i < rows * cols; i += BLOCK_THREADS) {
+        const int ly = i / cols, lx = i - ly * cols;
+        const int gy = clamp_index(by - R + ly, P.H - 1);
+        const int gx = wrap_index(bx - R + lx, P.W);
+        sm.ref[ly * TILE_PITCH + lx] = load_ref(P, gx, gy);
+    }
+    for (int i = threadIdx.x; i < rows; i += BLOCK_THREADS) {
+        const int gy = clamp_index(by - R + i, P.H - 1);
+        float s, c;
+        sincospif(0.5f - (2.0f * gy + 1.0f) / (2.0f * P.H), &s, &c);
+        sm.row_sin[i] = s;
+        sm.row_cos[i] = c;
+    }
+    for (int i = threadIdx.x; i < cols; i += BLOCK_THREADS) {
+        const int gx = wrap_index(bx - R + i, P.W);
+        float s, c;
+        sincospif((2.0f * gx + 1.0f) / P.W - 1.0f, &s, &c);
+        sm.col_sin[i] = s;
+        sm.col_cos[i] = c;
+    }
+}
+
+// Local (halo-inclusive) tile coordinates of the pixel: lx, ly.
+__device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const TileSmem& sm, int lx, int ly) {
+    RefStats st;
+    st.Ip = sm.ref[ly * TILE_PITCH + lx];
+    float Sw = 0.f, SI = 0.f;
+    for (int a = 0; a < P.K; ++a) {
+        const int oy = a * P.stride - P.radius;
+        for (int b = 0; b < P.K; ++b) {
+            const int ox = b * P.stride - P.radius;
+            const float Iq = sm.ref[(ly + oy) * TILE_PITCH + lx + ox];
+            const float dI = Iq - st.Ip;
+            const float w = exp2f(fmaf(P.wc, dI * dI, P.ws * (float)(ox * ox + oy * oy)));
+            Sw += w;
+            SI = fmaf(w, Iq, SI);
+        }
+    }
+    st.Sw = Sw;
+    st.mu = SI / Sw;
+    float SIc = 0.f, SIIc = 0.f;
+    for (int a = 0; a < P.K; ++a) {
+        const int oy = a * P.stride - P.radius;
+        for (int b = 0; b < P.K; ++b) {
+            const int ox = b * P.stride - P.radius;
+            const float Iq = sm.ref[(ly + oy) * TILE_PITCH + lx + ox];
+            const float dI = Iq - st.Ip;
+            const float w = exp2f(fmaf(P.wc, dI * dI, P.ws * (float)(ox * ox + oy * oy)));
+            const float Ic = Iq - st.mu;
+            SIc = fmaf(w, Ic, SIc);
+            SIIc = fmaf(w * Ic, Ic, SIIc);
+        }
+    }
+    st.SIc = SIc;
+    st.varI = Sw * SIIc - SIc * SIc;
+    return st;
+}
+
+// Cost of plane (range d along rp, unit normal n) at the pixel. Returns 2 for
+// an invalid plane (a patch ray meets it from behind or grazing).
+template <int NS>
+__device__ float plane_cost(const PixelParams& P, const TileSmem& sm, int lx, int ly, const RefStats& st,
+                            float3 rp, float d, float3 n) {
+    const float eps = 1e-8f * st.Sw * st.Sw;
+    if (st.varI < eps) return 2.0f;
+    const float dn = d * (n.x * rp.x + n.y * rp.y + n.z * rp.z);
+    const int K = P.K, R = P.radius, stp = P.stride, S = P.S;
+    const int ac = K >> 1;  // centre-most sample first: its intensity centres each view
+
+    float c0[NS], SJ[NS], SJJ[NS], SIJ[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        c0[s] = 0.f;
+        SJ[s] = 0.f;
+        SJJ[s] = 0.f;
+        SIJ[s] = 0.f;
+    }
+    bool valid = true;
+    // first sample
+    {
+        const int o = ac * stp - R;
+        const float cl = sm.row_cos[ly + o], sl = sm.row_sin[ly + o];
+        const float3 rq = make_float3(cl * sm.col_sin[lx + o], -sl, cl * sm.col_cos[lx + o]);
+        const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+        if (!(den < -1e-6f)) return 2.0f;
+        const float t = __fdividef(dn, den);
+        const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (s < S) {
+                const SourceView& V = P.src[s];
+                const float Yx = fmaf(V.R[0], X, fmaf(V.R[1], Y, fmaf(V.R[2], Z, V.t[0])));
+                const float Yy = fmaf(V.R[3], X, fmaf(V.R[4], Y, fmaf(V.R[5], Z, V.t[1])));
+                const float Yz = fmaf(V.R[6], X, fmaf(V.R[7], Y, fmaf(V.R[8], Z, V.t[2])));
+                float uc, vc;
+                project_dir(Yx, Yy, Yz, V.su, V.ou, V.sv, V.ov, uc, vc);
+                c0[s] = sample_bilinear(V.tex, V.inv_w, V.inv_h, uc, vc);
+            }
+        }
+    }
+    for (int a = 0; a < K && valid; ++a) {
+        const int oy = a * stp - R;
+        const float cl = sm.row_cos[ly + oy], sl = sm.row_sin[ly + oy];
+        const float* ref_row = sm.ref + (ly + oy) * TILE_PITCH + lx;
+        for (int b = 0; b < K; ++b) {
+            if (a == ac && b == ac) continue;
+            const int ox = b * stp - R;
+            const float Iq = ref_row[ox];
+            const float dI = Iq - st.Ip;
+            const float w = exp2f(fmaf(P.wc, dI * dI, P.ws * (float)(ox * ox + oy * oy)));
+            const float wI = w * (Iq - st.mu);
+            const float3 rq = make_float3(cl * sm.col_sin[lx + ox], -sl, cl * sm.col_cos[lx + ox]);
+            const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+            if (!(den < -1e-6f)) {
+                valid = false;
+                break;
+            }
+            const float t = __fdividef(dn, den);
+            const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                if (s < S) {
+                    const SourceView& V = P.src[s];
+                    const float Yx = fmaf(V.R[0], X, fmaf(V.R[1], Y, fmaf(V.R[2], Z, V.t[0])));
+                    const float Yy = fmaf(V.R[3], X, fmaf(V.R[4], Y, fmaf(V.R[5], Z, V.t[1])));
+                    const float Yz = fmaf(V.R[6], X, fmaf(V.R[7], Y, fmaf(V.R[8], Z, V.t[2])));
+                    float uc, vc;
+                    project_dir(Yx, Yy, Yz, V.su, V.ou, V.sv, V.ov, uc, vc);
+                    const float Jc = sample_bilinear(V.tex, V.inv_w, V.inv_h, uc, vc) - c0[s];
+                    const float tw = w * Jc;
+                    SJ[s] += tw;
+                    SJJ[s] = fmaf(tw, Jc, SJJ[s]);
+                    SIJ[s] = fmaf(wI, Jc, SIJ[s]);
+                }
+            }
+        }
+    }
+    if (!valid) return 2.0f;
+
+    float cs[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        float c = 3.0f;  // unused slots sort last
+        if (s < S) {
+            const float varJ = st.Sw * SJJ[s] - SJ[s] * SJ[s];
+            const float cov = st.Sw * SIJ[s] - st.SIc * SJ[s];
+            if (varJ < eps) {
+                c = 2.0f;
+            } else {
+                float ncc = cov * rsqrtf(st.varI * varJ);
+                ncc = fminf(1.0f, fmaxf(-1.0f, ncc));
+                c = 1.0f - ncc;
+            }
+        }
+        cs[s] = c;
+    }
+    // odd-even transposition sort, then the mean of the best_k smallest
+#pragma unroll
+    for (int pass = 0; pass < NS; ++pass) {
+#pragma unroll
+        for (int s = (pass & 1); s + 1 < NS; s += 2) {
+            const float lo = fminf(cs[s], cs[s + 1]), hi = fmaxf(cs[s], cs[s + 1]);
+            cs[s] = lo;
+            cs[s + 1] = hi;
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        if (s < P.best_k) sum += cs[s];
+    return sum / (float)P.best_k;
+}
+
+// Face the camera: n . r_p < 0 (|n . r_p| < 1e-3: replace by -r_p).
+__device__ __forceinline__ float3 face_camera(float3 n, float3 rp) {
+    const float c = n.x * rp.x + n.y * rp.y + n.z * rp.z;
+    if (fabsf(c) < 1e-3f) return make_float3(-rp.x, -rp.y, -rp.z);
+    if (c > 0.f) return make_float3(-n.x, -n.y, -n.z);
+    return n;
+}
+
+template <int NS, int MODE>
+__global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_constant__ PixelParams P) {
+    __shared__ TileSmem sm;
+    const int bx = blockIdx.x * TILE_W, by = blockIdx.y * TILE_H;
+    stage_tile(P, sm, bx, by);
+    __syncthreads();
+
+    const int tx = threadIdx.x % (TILE_W / 2), ty = threadIdx.x / (TILE_W / 2);
+    const int y = by + ty;
+    const int x = bx + 2 * tx + ((y + P.colour) & 1);
+    if (x >= P.W || y >= P.H) return;
+    const int lx = x - bx + P.radius, ly = y - by + P.radius;
+    const size_t N = (size_t)P.W * P.H;
+    const size_t i = (size_t)y * P.W + x;
+
+    const float3 rp = make_float3(sm.row_cos[ly] * sm.col_sin[lx], -sm.row_sin[ly],
+                                  sm.row_cos[ly] * sm.col_cos[lx]);
+    const RefStats st = ref_stats(P, sm, lx, ly);
+
+    if (MODE == MODE_COST) {
+        const float3 n = make_float3(P.nx[i], P.ny[i], P.nz[i]);
+        P.cost[i] = plane_cost<NS>(P, sm, lx, ly, st, rp, P.depth[i], n);
+        return;
+    }
+    if (MODE == MODE_INIT) {
+        const U4 u = draw_uniform4(i, 0, 0, P.seed, P.keyframe);
+        const float inv = fmaf(u.x, P.inv_dmin - P.inv_dmax, P.inv_dmax);
+        const float d = 1.0f / inv;
+        const float z = 1.0f - 2.0f * u.y;
+        const float rho = sqrtf(fmaxf(0.f, 1.0f - z * z));
+        float sp, cp;
+        sincospif(2.0f * u.z, &sp, &cp);
+        const float3 n = face_camera(make_float3(rho * cp, rho * sp, z), rp);
+        P.depth[i] = d;
+        P.nx[i] = n.x;
+        P.ny[i] = n.y;
+        P.nz[i] = n.z;
+        P.cost[i] = plane_cost<NS>(P, sm, lx, ly, st, rp, d, n);
+        return;
+    }
+
+    // MODE_SWEEP: propagation then refinement (Sec. III-C).
+    float bd = P.depth[i];
+    float3 bn = make_float3(P.nx[i], P.ny[i], P.nz[i]);
+    float bc = P.cost[i];
+    (void)N;
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const int qy = y + c_neighbors[P.table][k][1];
+        if (qy < 0 || qy >= P.H) continue;
+        const int qx = wrap_index(x + c_neighbors[P.table][k][0], P.W);
+        const size_t j = (size_t)qy * P.W + qx;
+        const float3 nq = make_float3(P.nx[j], P.ny[j], P.nz[j]);
+        const float den = nq.x * rp.x + nq.y * rp.y + nq.z * rp.z;
+        if (!(den < -1e-6f)) continue;
+        const float3 rq = pixel_bearing(qx, qy, P.W, P.H);
+        const float dc = P.depth[j] * (nq.x * rq.x + nq.y * rq.y + nq.z * rq.z) / den;
+        if (!(dc >= P.d_min && dc <= P.d_max)) continue;
+        const float c = plane_cost<NS>(P, sm, lx, ly, st, rp, dc, nq);
+        if (c < bc) {
+            bc = c;
+            bd = dc;
+            bn = nq;
+        }
+    }
+    const float span = P.inv_dmin - P.inv_dmax;
+#pragma unroll 1
+    for (int k = 0; k < P.n_refine; ++k) {
+        const float s = ldexpf(1.0f, -(k + 1));
+        const U4 u = draw_uniform4(i, (uint64_t)P.iter, (uint64_t)(1 + k), P.seed, P.keyframe);
+        float inv = fmaf((2.0f * u.x - 1.0f) * s, span, 1.0f / bd);
+        inv = fminf(P.inv_dmin, fmaxf(P.inv_dmax, inv));
+        const float dc = 1.0f / inv;
+        float3 nc = make_float3(fmaf(s, 2.0f * u.y - 1.0f, bn.x), fmaf(s, 2.0f * u.z - 1.0f, bn.y),
+                                fmaf(s, 2.0f * u.w - 1.0f, bn.z));
+        const float il = 1.0f / sqrtf(nc.x * nc.x + nc.y * nc.y + nc.z * nc.z);
+        nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
+        const float c = plane_cost<NS>(P, sm, lx, ly, st, rp, dc, nc);
+        if (c < bc) {
+            bc = c;
+            bd = dc;
+            bn = nc;
+        }
+    }
+    P.depth[i] = bd;
+    P.nx[i] = bn.x;
+    P.ny[i] = bn.y;
+    P.nz[i] = bn.z;
+    P.cost[i] = bc;
+}
+
+template <int NS>
+cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t stream) {
+    const dim3 grid((p.W + TILE_W - 1) / TILE_W, (p.H + TILE_H - 1) / TILE_H);
+    switch (mode) {
+        case MODE_COST: pixel_kernel<NS, MODE_COST><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
+        case MODE_INIT: pixel_kernel<NS, MODE_INIT><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
+        default: pixel_kernel<NS, MODE_SWEEP><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pmsp

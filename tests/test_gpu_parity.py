@@ -1,0 +1,305 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (the densification's own bar): per-pixel cost within 1e-4
+absolute and range within 0.5 % relative on at least 99.5 % of pixels; where
+both sides take the same decisions the agreement is far tighter and the
+tests say so. Several PatchMatch results can be correct: when two candidate
+planes' costs differ by less than the FP32 rounding of the cost, the CUDA path
+and the oracle may keep different ones, which is why whole runs are compared
+by fraction.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+COST_TOL = 1e-4
+DEPTH_TOL = 5e-3
+
+
+@pytest.fixture(scope="module")
+def pm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2211_16266_gb300 as pm
+    return pm
+
+
+@pytest.fixture(scope="module")
+def ctx(pm):
+    import torch
+    c = pm.Context(0, stream=torch.cuda.current_stream())
+    yield c
+    c.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _problem(name):
+    if name == "c0":
+        return scenes.config0()
+    if name == "mid6":
+        p = scenes.config1(W=384, H=192)
+        return p
+    if name == "ragged":
+        p = scenes.trajectory_problem(250, 131, 3, seed_scene=1010)
+        p.params = dict(d_min=0.3, d_max=10.0, patch_w=9, patch_stride=3, iterations=3, best_k=2,
+                        sigma_color=0.15, sigma_space=4.0, n_refine=6, neighbor_table=1, seed=5,
+                        keyframe_id=77)
+        return p
+    if name == "mid6_f16":
+        p = scenes.config1(W=384, H=192)
+        p2 = scenes.trajectory_problem(384, 192, 6, fmt="f16")
+        p2.params = p.params
+        return p2
+    if name == "tiny":
+        p = scenes.trajectory_problem(8, 4, 1, seed_scene=1011)
+        p.params = dict(d_min=0.3, d_max=10.0, patch_w=5, patch_stride=1, iterations=2, best_k=1,
+                        sigma_color=0.0, sigma_space=0.0, n_refine=6, neighbor_table=0, seed=1,
+                        keyframe_id=2)
+        return p
+    raise KeyError(name)
+
+
+def _gpu_args(prob):
+    return (_dev(prob.ref.image), (prob.ref.R, prob.ref.t), [_dev(f.image) for f in prob.srcs],
+            [(f.R, f.t) for f in prob.srcs])
+
+
+def _maps_from(pm, d, n, c):
+    import torch
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    return pm.Maps(f(d), f(n), f(c))
+
+
+# ------------------------------------------------------------------ sampling
+
+@pytest.mark.parametrize("fmt", ["u8", "f16", "f32"])
+def test_bilinear_sample_matches_oracle(pm, ctx, fmt):
+    rng = np.random.default_rng(0)
+    H, W = 37, 64
+    base = rng.uniform(0, 1, size=(H, W))
+    img = {"u8": (base * 255).astype(np.uint8), "f16": base.astype(np.float16),
+           "f32": base.astype(np.float32)}[fmt]
+    uc = np.concatenate([rng.uniform(-0.5, W - 0.5, 2000), [-0.5, -0.25, W - 0.5, W - 0.75, 0, W - 1],
+                         rng.uniform(-0.5, W - 0.5, 6)]).astype(np.float32)
+    vc = np.concatenate([rng.uniform(-0.5, H - 0.5, 2000), [10, 3, 7, 20, -0.5, H - 0.5],
+                         [-0.5, -0.3, H - 0.5, H - 0.6, 0.0, H - 1.0]]).astype(np.float32)
+    got = pm.pmsp_sample_bilinear(ctx, _dev(img), _dev(uc), _dev(vc)).cpu().numpy()
+    want = np.array([oracle.sample(img, float(u), float(v)) for u, v in zip(uc, vc)])
+    assert np.max(np.abs(got - want)) < 2e-6
+    # host memory path gives the same numbers
+    got_h = pm.pmsp_sample_bilinear(ctx, img, uc, vc)
+    assert np.array_equal(got_h, got)
+
+
+# ---------------------------------------------------------------------- cost
+
+@pytest.mark.parametrize("name", ["c0", "mid6", "ragged", "mid6_f16", "tiny"])
+def test_cost_of_given_planes(pm, ctx, name):
+    prob = _problem(name)
+    pb = oracle.Problem.from_scene(prob)
+    d, n, _ = pb.init()
+    # a second family of planes: ground-truth range, normals facing the camera
+    d = d.astype(np.float32).astype(np.float64)
+    n = n.astype(np.float32).astype(np.float64)
+    want = pb.cost_map(d, n)
+    maps = _maps_from(pm, d, n, np.zeros_like(d))
+    pm.pmsp_cost_map(ctx, *_gpu_args(prob), prob.params, maps)
+    got = maps.cost.cpu().numpy().astype(np.float64)
+    err = np.abs(got - want)
+    assert np.mean(err <= COST_TOL) >= 0.999, (np.mean(err <= COST_TOL), err.max())
+    assert np.median(err) < 1e-5
+
+    gt = prob.ref.range
+    H, W = gt.shape
+    r = np.stack([oracle.bearing(W, H, u, v) for v in range(H) for u in range(W)], 1).reshape(3, H, W)
+    n2 = -r
+    d2 = np.clip(gt, prob.params["d_min"], prob.params["d_max"]).astype(np.float32).astype(np.float64)
+    n2 = n2.astype(np.float32).astype(np.float64)
+    want2 = pb.cost_map(d2, n2)
+    maps2 = _maps_from(pm, d2, n2, np.zeros_like(d2))
+    pm.pmsp_cost_map(ctx, *_gpu_args(prob), prob.params, maps2)
+    err2 = np.abs(maps2.cost.cpu().numpy() - want2)
+    assert np.mean(err2 <= COST_TOL) >= 0.999, (np.mean(err2 <= COST_TOL), err2.max())
+
+
+# ---------------------------------------------------------------------- init
+
+@pytest.mark.parametrize("name", ["c0", "mid6", "ragged"])
+def test_random_init(pm, ctx, name):
+    prob = _problem(name)
+    pb = oracle.Problem.from_scene(prob)
+    d0, n0, c0 = pb.init()
+    m = pm.pmsp_init(ctx, *_gpu_args(prob), prob.params)
+    d, n, c = (a.cpu().numpy().astype(np.float64) for a in (m.depth, m.normal, m.cost))
+    assert np.max(np.abs(d - d0) / d0) < 1e-5
+    same_n = np.all(np.abs(n - n0) < 1e-5, axis=0)
+    assert np.mean(same_n) >= 0.999
+    assert np.mean(np.abs(c - c0) <= COST_TOL) >= 0.995
+
+
+# ---------------------------------------------------------------- half-sweep
+
+@pytest.mark.parametrize("name", ["c0", "mid6", "ragged", "tiny"])
+def test_one_halfsweep_from_shared_state(pm, ctx, name):
+    prob = _problem(name)
+    pb = oracle.Problem.from_scene(prob)
+    d, n, c = pb.init()
+    # a first sweep on the oracle gives a less trivial shared state
+    pb.halfsweep(d, n, c, 0, 0)
+    d = d.astype(np.float32).astype(np.float64)
+    n = n.astype(np.float32).astype(np.float64)
+    c = c.astype(np.float32).astype(np.float64)
+    for colour, it in ((1, 0), (0, 1)):
+        state = _maps_from(pm, d, n, c)
+        pm.pmsp_halfsweep(ctx, *_gpu_args(prob), prob.params, colour, it, state)
+        gd, gn, gc = (a.cpu().numpy().astype(np.float64) for a in (state.depth, state.normal, state.cost))
+        od, on, oc = d.copy(), n.copy(), c.copy()
+        pb.halfsweep(od, on, oc, colour, it)
+        H, W = d.shape
+        other = ((np.arange(W)[None, :] + np.arange(H)[:, None]) % 2) != colour
+        assert np.array_equal(gd[other], d[other]) and np.array_equal(gc[other], c[other])
+        act = ~other
+        assert np.mean(np.abs(gc - oc)[act] <= COST_TOL) >= 0.995
+        assert np.mean((np.abs(gd - od) / od)[act] <= DEPTH_TOL) >= 0.995
+        # costs never rise
+        assert np.all(gc[act] <= c[act] + 1e-6)
+        d, n, c = od, on, oc
+
+
+# ------------------------------------------------------------------ densify
+
+@pytest.mark.parametrize("name", ["c0", "mid6"])
+def test_densify_matches_oracle(pm, ctx, name):
+    prob = _problem(name)
+    pb = oracle.Problem.from_scene(prob)
+    od, on, oc = pb.densify()
+    m = pm.pmsp_densify(ctx, *_gpu_args(prob), prob.params)
+    gd, gn, gc = (a.cpu().numpy().astype(np.float64) for a in (m.depth, m.normal, m.cost))
+    depth_ok = np.abs(gd - od) / od <= DEPTH_TOL
+    cost_ok = np.abs(gc - oc) <= COST_TOL
+    gt = prob.ref.range
+    gt_gpu = np.mean(np.abs(gd - gt) / gt < 0.05)
+    gt_orc = np.mean(np.abs(od - gt) / gt < 0.05)
+    print(f"{name}: depth parity {depth_ok.mean():.4f} cost parity {cost_ok.mean():.4f} "
+          f"GT<5%: gpu {gt_gpu:.4f} oracle {gt_orc:.4f}")
+    assert depth_ok.mean() >= 0.995
+    assert cost_ok.mean() >= 0.995
+    assert abs(gt_gpu - gt_orc) < 0.01
+
+
+def test_densify_host_and_device_paths_agree(pm, ctx):
+    prob = _problem("c0")
+    m_dev = pm.pmsp_densify(ctx, *_gpu_args(prob), prob.params)
+    m_host = pm.pmsp_densify(ctx, prob.ref.image, (prob.ref.R, prob.ref.t), [f.image for f in prob.srcs],
+                             [(f.R, f.t) for f in prob.srcs], prob.params)
+    for a, b in zip(m_dev.numpy(), m_host.numpy()):
+        assert np.array_equal(a, b)
+
+
+def test_densify_is_deterministic(pm, ctx):
+    prob = _problem("mid6")
+    a = pm.pmsp_densify(ctx, *_gpu_args(prob), prob.params).numpy()
+    b = pm.pmsp_densify(ctx, *_gpu_args(prob), prob.params).numpy()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+# -------------------------------------------------------------------- filter
+
+def test_consistency_filter_matches_oracle(pm, ctx):
+    W, H = 384, 192
+    traj = scenes.trajectory(5, seed=2000)
+    scene = scenes.Scene(seed=1001)
+    scene.objects = scenes.place_objects(1078, [c for _, _, c in traj], n=20)
+    rng = np.random.default_rng(9)
+    maps, poses = [], []
+    for (R, t, C) in traj:
+        _, rg = scene.render(R, t, W, H, ss=1)
+        noisy = rg * (1 + rng.normal(0, 0.01, size=rg.shape))
+        noisy[rng.uniform(size=rg.shape) < 0.05] = 0.0
+        maps.append(noisy.astype(np.float32))
+        poses.append((R, t))
+    ref, nb = maps[2], [maps[i] for i in (0, 1, 3, 4)]
+    nbp = [poses[i] for i in (0, 1, 3, 4)]
+    o_out, o_agree, margin = oracle.consistency_filter(ref.astype(np.float64), poses[2],
+                                                       [m.astype(np.float64) for m in nb], nbp, 1.0, 2)
+    g_out, g_agree = pm.pmsp_consistency_filter(ctx, _dev(ref), poses[2], [_dev(m) for m in nb], nbp, 1.0, 2)
+    g_out, g_agree = g_out.cpu().numpy(), g_agree.cpu().numpy()
+    clear = margin > 1e-3
+    assert np.array_equal(g_agree[clear], o_agree[clear])
+    assert np.array_equal(g_out[clear] > 0, o_out[clear] > 0)
+    assert np.mean(clear) > 0.98
+    assert np.array_equal(g_out[g_out > 0], ref[g_out > 0])
+    # host path and in-place output
+    h_out, h_agree = pm.pmsp_consistency_filter(ctx, ref, poses[2], nb, nbp, 1.0, 2)
+    assert np.array_equal(h_out, g_out) and np.array_equal(h_agree, g_agree)
+    inplace = _dev(ref)
+    pm.pmsp_consistency_filter(ctx, inplace, poses[2], [_dev(m) for m in nb], nbp, 1.0, 2, out=inplace)
+    assert np.array_equal(inplace.cpu().numpy(), g_out)
+
+
+# ---------------------------------------------------------------- API errors
+
+def test_invalid_arguments_are_rejected(pm, ctx):
+    prob = _problem("c0")
+    args = _gpu_args(prob)
+    bad = [dict(prob.params, best_k=3), dict(prob.params, patch_w=8), dict(prob.params, patch_w=23),
+           dict(prob.params, d_min=0.0), dict(prob.params, d_min=5.0, d_max=2.0),
+           dict(prob.params, patch_stride=0), dict(prob.params, neighbor_table=2)]
+    for p in bad:
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_densify(ctx, *args, p)
+        assert e.value.code == pm.PMSP_EINVAL
+    odd = _dev(prob.ref.image[:, :-1])
+    with pytest.raises(pm.PmspError) as e:
+        pm.pmsp_densify(ctx, odd, args[1], args[2], args[3], prob.params)
+    assert e.value.code == pm.PMSP_EINVAL
+    wrong = pm.Maps.empty(10, 10, device="cuda")
+    with pytest.raises(pm.PmspError):
+        pm.pmsp_densify(ctx, *args, prob.params, out=wrong)
+    # the context stays usable
+    pm.pmsp_densify(ctx, *args, dict(prob.params, iterations=1))
+    pm.pmsp_sync(ctx)
+
+
+# ---------------------------------------------- full size, sampled parity
+
+def test_full_size_sampled_parity(pm, ctx):
+    """1920x960, 6 sources, 11x11/2, 8 iterations (the benchmarked launch
+    configuration): the stored cost of sampled pixels is the oracle's cost of
+    the stored plane, and one more half-sweep agrees pixel by pixel."""
+    prob = scenes.config1()
+    args = _gpu_args(prob)
+    m = pm.pmsp_densify(ctx, *args, prob.params)
+    d, n, c = (a.cpu().numpy().astype(np.float64) for a in (m.depth, m.normal, m.cost))
+    pb = oracle.Problem.from_scene(prob)
+    H, W = d.shape
+    rng = np.random.default_rng(4)
+    us, vs = rng.integers(0, W, 1500), rng.integers(0, H, 1500)
+    errs = np.array([abs(pb.cost(u, v, d[v, u], n[:, v, u]) - c[v, u]) for u, v in zip(us, vs)])
+    assert np.mean(errs <= COST_TOL) >= 0.995
+    gt = prob.ref.range
+    print(f"full size: GT within 5% {np.mean(np.abs(d - gt) / gt < 0.05):.4f}")
+    # one more half-sweep from the GPU state
+    state = _maps_from(pm, d, n, c)
+    pm.pmsp_halfsweep(ctx, *args, prob.params, 0, 8, state)
+    gd, gc = state.depth.cpu().numpy(), state.cost.cpu().numpy()
+    ok_c, ok_d = [], []
+    for u, v in zip(us[:600], vs[:600]):
+        u = int(u) - ((int(u) + int(v)) & 1)
+        if u < 0:
+            u += 2
+        od, on, oc = pb.update_pixel(d, n, c, u, int(v), 8)
+        ok_c.append(abs(oc - gc[v, u]) <= COST_TOL)
+        ok_d.append(abs(od - gd[v, u]) / od <= DEPTH_TOL)
+    assert np.mean(ok_c) >= 0.995 and np.mean(ok_d) >= 0.995
