@@ -198,7 +198,7 @@ def run_gpu(args):
     sweep_ms = time_sweeps(pm, ctx, stream, kf_args, params, out, flush)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    e2e = run_e2e(pm, ctx, stream, frames, KF, NB, nb_maps, params, args)
+    e2e = None if args.no_e2e else run_e2e(pm, ctx, stream, frames, KF, NB, nb_maps, params, args)
 
     evals, vs = algorithmic_counts()
     clocks = clk.summary() or {}
@@ -331,6 +331,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -194,6 +194,18 @@ int pmsp_consistency_filter(pmsp_ctx* ctx, const pmsp_maps* ref, const pmsp_pose
 int pmsp_sample_bilinear(pmsp_ctx* ctx, const pmsp_image* img, int n, const float* uc,
                          const float* vc, float* out);
 
+/*
+ * Equirectangular projection (Sec. III-C camera model) of n directions into a
+ * W x H panorama, as the cost and the filter compute it on the device:
+ * lon = atan2(x, z), lat = atan2(-y, hypot(x, z)), u_c = W (lon + pi) / 2pi - 0.5,
+ * v_c = H (pi/2 - lat) / pi - 0.5.
+ *   dirs     3n floats (x, y, z interleaved), any length > 0
+ *   uc, vc   n floats each, written
+ *   memory   pmsp_memory of all three arrays
+ */
+int pmsp_project(pmsp_ctx* ctx, int W, int H, int n, const float* dirs, float* uc, float* vc,
+                 int memory);
+
 #ifdef __cplusplus
 }
 #endif

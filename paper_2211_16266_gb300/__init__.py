@@ -97,6 +97,7 @@ _SIGS = {
     "pmsp_consistency_filter": ([_P, _M, _O, _M, _O, ctypes.c_int, ctypes.c_float, ctypes.c_int, _M, _F],
                                 ctypes.c_int),
     "pmsp_sample_bilinear": ([_P, _I, ctypes.c_int, _F, _F, _F], ctypes.c_int),
+    "pmsp_project": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _F, _F, _F, ctypes.c_int], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -356,3 +357,20 @@ def pmsp_sample_bilinear(ctx, img, uc, vc):
         out = np.zeros_like(uc)
     ctx.check(_lib.pmsp_sample_bilinear(ctx.h, ctypes.byref(im), int(uc.shape[0]), _ptr(uc), _ptr(vc), _ptr(out)))
     return out
+
+
+def pmsp_project(ctx, W, H, dirs):
+    """Continuous pixel coordinates (uc, vc) of (n, 3) directions in a W x H panorama."""
+    if _is_torch(dirs):
+        import torch
+        d = dirs.contiguous()
+        uc = torch.empty(d.shape[0], dtype=torch.float32, device=d.device)
+        vc = torch.empty_like(uc)
+        mem = PMSP_DEVICE if d.is_cuda else PMSP_HOST
+    else:
+        d = np.ascontiguousarray(dirs, dtype=np.float32).reshape(-1, 3)
+        uc = np.zeros(d.shape[0], np.float32)
+        vc = np.zeros_like(uc)
+        mem = PMSP_HOST
+    ctx.check(_lib.pmsp_project(ctx.h, int(W), int(H), int(d.shape[0]), _ptr(d), _ptr(uc), _ptr(vc), mem))
+    return uc, vc

@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+#include "atan_coeffs.cuh"
+
 namespace pmsp {
 
 // Unit bearing of pixel centre (u, v). sincospif keeps the angle exact up to
@@ -20,14 +22,59 @@ __device__ __forceinline__ float3 pixel_bearing(int u, int v, int W, int H) {
     return make_float3(cl * sn, -sl, cl * cn);
 }
 
-// Continuous pixel coordinates (integers at pixel centres) of direction Y in a
-// camera whose scale/offset pair maps longitude and latitude to u_c and v_c.
-__device__ __forceinline__ void project_dir(float X, float Y, float Z, float su, float ou, float sv,
-                                            float ov, float& uc, float& vc) {
-    const float lon = atan2f(X, Z);
-    const float lat = atan2f(-Y, sqrtf(fmaf(X, X, Z * Z)));
+// 2^x for x <= 0 on the special-function unit (relative error ~2^-22).
+__device__ __forceinline__ float exp2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// atan(mn / mx) for 0 <= mn <= mx: the Remez-fitted odd polynomial
+// r * P(r^2) of atan_coeffs.cuh (|error| below 1.3e-7 rad in FP32). mx = 0
+// (the origin) gives 0.
+__device__ __forceinline__ float atan_reduced(float mn, float mx) {
+    const float r = __fdividef(mn, fmaxf(mx, 1e-30f));
+    return r * atan_poly(r * r);
+}
+
+// Four-quadrant arctangent by octant reduction and reflection
+// (pi/2 - a for |y| > |x|, pi - a for x < 0, sign of y). Matches atan2 on
+// the axes, at the origin and for signed zeros.
+__device__ __forceinline__ float fast_atan2(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    float a = atan_reduced(fminf(ax, ay), fmaxf(ax, ay));
+    a = ay > ax ? 1.57079632679489662f - a : a;
+    a = x < 0.f ? 3.14159265358979324f - a : a;
+    return copysignf(a, y);
+}
+
+// The same for x >= 0 (half plane: no reflection about the y axis).
+__device__ __forceinline__ float fast_atan2_xpos(float y, float x) {
+    const float ay = fabsf(y);
+    float a = atan_reduced(fminf(x, ay), fmaxf(x, ay));
+    a = ay > x ? 1.57079632679489662f - a : a;
+    return copysignf(a, y);
+}
+
+// Continuous pixel coordinates (integers at pixel centres) of direction
+// (X, Y, Z), any length > 0, in a camera whose scale/offset pairs map
+// longitude and latitude to u_c and v_c: lon = atan2(X, Z),
+// lat = atan2(-Y, hypot(X, Z)); hypot as q * rsqrt(q), exact 0 at the poles.
+__device__ __forceinline__ void project_dir_fast(float X, float Y, float Z, float su, float ou, float sv,
+                                                 float ov, float& uc, float& vc) {
+    const float lon = fast_atan2(X, Z);
+    const float q = fmaf(X, X, Z * Z);
+    const float rho = q * rsqrtf(fmaxf(q, 1e-30f));
+    const float lat = fast_atan2_xpos(-Y, rho);
     uc = fmaf(lon, su, ou);
     vc = fmaf(lat, sv, ov);
+}
+
+// floor(x) for |x| < 2^22 with two FP32 adds: adding 1.5 * 2^23 rounded
+// towards -inf leaves floor(x) in the low mantissa bits.
+__device__ __forceinline__ float floor_small(float x) {
+    const float M = 12582912.0f;
+    return __fadd_rd(x, M) - M;
 }
 
 // Bilinear fetch at (uc, vc): columns floor(uc), floor(uc)+1 wrapped, rows
@@ -39,7 +86,7 @@ __device__ __forceinline__ void project_dir(float X, float Y, float Z, float su,
 // z = (i0+1, j0), w = (i0, j0).
 __device__ __forceinline__ float sample_bilinear(cudaTextureObject_t tex, float inv_w, float inv_h,
                                                  float uc, float vc) {
-    const float fi = floorf(uc), fj = floorf(vc);
+    const float fi = floor_small(uc), fj = floor_small(vc);
     const float fx = uc - fi, fy = vc - fj;
     const float4 g = tex2Dgather<float4>(tex, fmaf(fi, inv_w, inv_w), fmaf(fj, inv_h, inv_h), 0);
     const float top = fmaf(fx, g.z - g.w, g.w);

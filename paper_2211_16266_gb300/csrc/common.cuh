@@ -78,6 +78,8 @@ struct FilterParams {
 // Launchers (one translation unit per source-count bucket).
 cudaError_t launch_pixel_kernel(const PixelParams& p, int mode, cudaStream_t stream);
 cudaError_t launch_filter_kernel(const FilterParams& p, cudaStream_t stream);
+cudaError_t launch_project_kernel(int W, int H, int n, const float* dirs, float* uc, float* vc,
+                                  cudaStream_t stream);
 cudaError_t launch_sample_kernel(cudaTextureObject_t tex, int W, int H, int n, const float* uc,
                                  const float* vc, float* out, cudaStream_t stream);
 

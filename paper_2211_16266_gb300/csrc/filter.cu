@@ -1,4 +1,5 @@
-// Geometric-consistency filter kernel and the standalone bilinear fetch kernel.
+// Geometric-consistency filter kernel and the standalone camera-model kernels
+// (bilinear fetch, projection) behind pmsp_sample_bilinear and pmsp_project.
 //
 // Paper Sec. III: once five depth maps are available the current one is
 // checked against its neighbours' depth maps and outliers are removed. A
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Fil
             const FilterView& V = P.nb[j];
             const float3 Y = apply(V.Rf, V.tf, X);
             float uc, vc;
-            project_dir(Y.x, Y.y, Y.z, V.W * 0.15915494309189535f, 0.5f * V.W - 0.5f,
+            project_dir_fast(Y.x, Y.y, Y.z, V.W * 0.15915494309189535f, 0.5f * V.W - 0.5f,
                         -V.H * 0.3183098861837907f, 0.5f * V.H - 0.5f, uc, vc);
             const int ui = wrap_index((int)floorf(uc + 0.5f), V.W);
             const int vi = clamp_index((int)floorf(vc + 0.5f), V.H - 1);
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Fil
             const float3 rq = pixel_bearing(ui, vi, V.W, V.H);
             const float3 Z = apply(V.Rb, V.tb, make_float3(dj * rq.x, dj * rq.y, dj * rq.z));
             float u2, v2;
-            project_dir(Z.x, Z.y, Z.z, su, ou, sv, ov, u2, v2);
+            project_dir_fast(Z.x, Z.y, Z.z, su, ou, sv, ov, u2, v2);
             float du = u2 - (float)x;
             du -= P.W * floorf(du / P.W + 0.5f);
             const float dv = v2 - (float)y;
@@ -70,6 +71,20 @@ cudaError_t launch_sample_kernel(cudaTextureObject_t tex, int W, int H, int n, c
                                  const float* vc, float* out, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
     sample_kernel<<<(n + 255) / 256, 256, 0, stream>>>(tex, 1.0f / W, 1.0f / H, n, uc, vc, out);
+    return cudaGetLastError();
+}
+
+__global__ void project_kernel(int n, const float* dirs, float su, float ou, float sv, float ov, float* uc,
+                               float* vc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) project_dir_fast(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], su, ou, sv, ov, uc[i], vc[i]);
+}
+
+cudaError_t launch_project_kernel(int W, int H, int n, const float* dirs, float* uc, float* vc,
+                                  cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    project_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, dirs, W * 0.15915494309189535f, 0.5f * W - 0.5f,
+                                                        -H * 0.3183098861837907f, 0.5f * H - 0.5f, uc, vc);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
-// Instantiation of the per-pixel kernels for up to 6 source views.
+// Instantiation of the per-pixel kernels for exactly 6 source views.
 #include "pixel_kernel.cuh"
 
 namespace pmsp {
-template cudaError_t launch_pixel_kernel_ns<6>(const PixelParams&, int, cudaStream_t);
+template cudaError_t launch_pixel_kernel_ns<6, true>(const PixelParams&, int, cudaStream_t);
 }  // namespace pmsp

@@ -1,6 +1,6 @@
 // Per-pixel PatchMatch kernels: matching cost, random initialisation and the
 // red-black half-sweep (propagation + refinement), templated on the number
-// of source views the block keeps in registers.
+// of source views the thread keeps in registers.
 //
 // Paper: random initialisation of the plane map (Sec. III-B); parallel
 // red-black propagation over an 8-neighbourhood whose inner neighbours sit
@@ -11,12 +11,14 @@
 // views (the cost of the PatchMatch works the paper cites).
 //
 // Design: one thread per active pixel of a 32x8 tile (one colour per launch).
-// The reference tile with its halo and the per-row / per-column bearing terms
-// are staged in shared memory; the sample loop runs over the patch with all
-// views innermost, so the plane intersection and the bilateral weight of a
-// sample are shared by every view. Per view four FP32 sums are kept: the
-// source intensity is centred on its value at the first (centre-most)
-// sample, which keeps the variance term free of cancellation.
+// The reference tile with its halo, the per-row / per-column bearing terms
+// and the spatial weights are staged in shared memory; the sample loop runs
+// over the patch with all views innermost, so the plane intersection and the
+// bilateral weight of a sample are shared by every view. Per view four FP32
+// sums are kept: the source intensity is centred on its value at the first
+// (centre-most) sample, which keeps the variance term free of cancellation.
+// The 8 neighbour candidates and the refinement candidates run through one
+// loop with a single inlined copy of the cost.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -33,11 +35,13 @@ static __constant__ int c_neighbors[2][8][2] = {
 
 constexpr int TILE_PITCH = TILE_W + 2 * MAX_HALO;
 constexpr int TILE_ROWS = TILE_H + 2 * MAX_HALO;
+constexpr int MAX_K = 2 * MAX_HALO + 1;
 
 struct TileSmem {
     float ref[TILE_ROWS * TILE_PITCH];  // normalised intensities, halo included
     float row_cos[TILE_ROWS], row_sin[TILE_ROWS];    // cos lat, sin lat
     float col_sin[TILE_PITCH], col_cos[TILE_PITCH];  // sin lon, cos lon
+    float wsp[MAX_K];                                // spatial log2-weight of offset index k
 };
 
 // Reference-side constants of one pixel (independent of the hypothesis).
@@ -79,20 +83,30 @@ __device__ __forceinline__ void stage_tile(const PixelParams& P, TileSmem& sm, i
         sm.col_sin[i] = s;
         sm.col_cos[i] = c;
     }
+    for (int k = threadIdx.x; k < P.K; k += BLOCK_THREADS) {
+        const float o = (float)(k * P.stride - R);
+        sm.wsp[k] = P.ws * o * o;
+    }
+}
+
+// Bilateral weight of sample (a, b) with intensity Iq: 2^(wc dI^2 + ws |o|^2).
+__device__ __forceinline__ float bilateral(const PixelParams& P, const TileSmem& sm, int a, int b, float Iq,
+                                           float Ip) {
+    const float dI = Iq - Ip;
+    return exp2_approx(fmaf(P.wc, dI * dI, sm.wsp[a] + sm.wsp[b]));
 }
 
 // Local (halo-inclusive) tile coordinates of the pixel: lx, ly.
 __device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const TileSmem& sm, int lx, int ly) {
     RefStats st;
     st.Ip = sm.ref[ly * TILE_PITCH + lx];
+    const int R = P.radius, stp = P.stride;
     float Sw = 0.f, SI = 0.f;
     for (int a = 0; a < P.K; ++a) {
-        const int oy = a * P.stride - P.radius;
+        const float* row = sm.ref + (ly + a * stp - R) * TILE_PITCH + lx - R;
         for (int b = 0; b < P.K; ++b) {
-            const int ox = b * P.stride - P.radius;
-            const float Iq = sm.ref[(ly + oy) * TILE_PITCH + lx + ox];
-            const float dI = Iq - st.Ip;
-            const float w = exp2f(fmaf(P.wc, dI * dI, P.ws * (float)(ox * ox + oy * oy)));
+            const float Iq = row[b * stp];
+            const float w = bilateral(P, sm, a, b, Iq, st.Ip);
             Sw += w;
             SI = fmaf(w, Iq, SI);
         }
@@ -101,12 +115,10 @@ __device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const TileSm
     st.mu = SI / Sw;
     float SIc = 0.f, SIIc = 0.f;
     for (int a = 0; a < P.K; ++a) {
-        const int oy = a * P.stride - P.radius;
+        const float* row = sm.ref + (ly + a * stp - R) * TILE_PITCH + lx - R;
         for (int b = 0; b < P.K; ++b) {
-            const int ox = b * P.stride - P.radius;
-            const float Iq = sm.ref[(ly + oy) * TILE_PITCH + lx + ox];
-            const float dI = Iq - st.Ip;
-            const float w = exp2f(fmaf(P.wc, dI * dI, P.ws * (float)(ox * ox + oy * oy)));
+            const float Iq = row[b * stp];
+            const float w = bilateral(P, sm, a, b, Iq, st.Ip);
             const float Ic = Iq - st.mu;
             SIc = fmaf(w, Ic, SIc);
             SIIc = fmaf(w * Ic, Ic, SIIc);
@@ -117,60 +129,58 @@ __device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const TileSm
     return st;
 }
 
+// Intensity of source view V at the projection of reference-frame point X.
+__device__ __forceinline__ float view_sample(const SourceView& V, float X, float Y, float Z) {
+    const float Yx = fmaf(V.R[0], X, fmaf(V.R[1], Y, fmaf(V.R[2], Z, V.t[0])));
+    const float Yy = fmaf(V.R[3], X, fmaf(V.R[4], Y, fmaf(V.R[5], Z, V.t[1])));
+    const float Yz = fmaf(V.R[6], X, fmaf(V.R[7], Y, fmaf(V.R[8], Z, V.t[2])));
+    float uc, vc;
+    project_dir_fast(Yx, Yy, Yz, V.su, V.ou, V.sv, V.ov, uc, vc);
+    return sample_bilinear(V.tex, V.inv_w, V.inv_h, uc, vc);
+}
+
 // Cost of plane (range d along rp, unit normal n) at the pixel. Returns 2 for
-// an invalid plane (a patch ray meets it from behind or grazing).
-template <int NS>
-__device__ float plane_cost(const PixelParams& P, const TileSmem& sm, int lx, int ly, const RefStats& st,
-                            float3 rp, float d, float3 n) {
+// an invalid plane (a patch ray meets it from behind or grazing). NS views
+// are kept in registers; EXACT means S == NS (no per-view guard).
+template <int NS, bool EXACT>
+__device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem& sm, int lx, int ly,
+                                            const RefStats& st, float3 rp, float d, float3 n) {
     const float eps = 1e-8f * st.Sw * st.Sw;
     if (st.varI < eps) return 2.0f;
     const float dn = d * (n.x * rp.x + n.y * rp.y + n.z * rp.z);
-    const int K = P.K, R = P.radius, stp = P.stride, S = P.S;
+    const int K = P.K, R = P.radius, stp = P.stride;
     const int ac = K >> 1;  // centre-most sample first: its intensity centres each view
 
     float c0[NS], SJ[NS], SJJ[NS], SIJ[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        c0[s] = 0.f;
-        SJ[s] = 0.f;
-        SJJ[s] = 0.f;
-        SIJ[s] = 0.f;
-    }
-    bool valid = true;
-    // first sample
     {
         const int o = ac * stp - R;
-        const float cl = sm.row_cos[ly + o], sl = sm.row_sin[ly + o];
-        const float3 rq = make_float3(cl * sm.col_sin[lx + o], -sl, cl * sm.col_cos[lx + o]);
+        const float cl = sm.row_cos[ly + o];
+        const float3 rq = make_float3(cl * sm.col_sin[lx + o], -sm.row_sin[ly + o], cl * sm.col_cos[lx + o]);
         const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
         if (!(den < -1e-6f)) return 2.0f;
         const float t = __fdividef(dn, den);
         const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            if (s < S) {
-                const SourceView& V = P.src[s];
-                const float Yx = fmaf(V.R[0], X, fmaf(V.R[1], Y, fmaf(V.R[2], Z, V.t[0])));
-                const float Yy = fmaf(V.R[3], X, fmaf(V.R[4], Y, fmaf(V.R[5], Z, V.t[1])));
-                const float Yz = fmaf(V.R[6], X, fmaf(V.R[7], Y, fmaf(V.R[8], Z, V.t[2])));
-                float uc, vc;
-                project_dir(Yx, Yy, Yz, V.su, V.ou, V.sv, V.ov, uc, vc);
-                c0[s] = sample_bilinear(V.tex, V.inv_w, V.inv_h, uc, vc);
-            }
+            c0[s] = 0.f;
+            SJ[s] = 0.f;
+            SJJ[s] = 0.f;
+            SIJ[s] = 0.f;
+            if (EXACT || s < P.S) c0[s] = view_sample(P.src[s], X, Y, Z);
         }
     }
+    bool valid = true;
     for (int a = 0; a < K && valid; ++a) {
         const int oy = a * stp - R;
-        const float cl = sm.row_cos[ly + oy], sl = sm.row_sin[ly + oy];
-        const float* ref_row = sm.ref + (ly + oy) * TILE_PITCH + lx;
+        const float cl = sm.row_cos[ly + oy], msl = -sm.row_sin[ly + oy];
+        const float* ref_row = sm.ref + (ly + oy) * TILE_PITCH + lx - R;
         for (int b = 0; b < K; ++b) {
             if (a == ac && b == ac) continue;
-            const int ox = b * stp - R;
-            const float Iq = ref_row[ox];
-            const float dI = Iq - st.Ip;
-            const float w = exp2f(fmaf(P.wc, dI * dI, P.ws * (float)(ox * ox + oy * oy)));
+            const float Iq = ref_row[b * stp];
+            const float w = bilateral(P, sm, a, b, Iq, st.Ip);
             const float wI = w * (Iq - st.mu);
-            const float3 rq = make_float3(cl * sm.col_sin[lx + ox], -sl, cl * sm.col_cos[lx + ox]);
+            const int cx = lx + b * stp - R;
+            const float3 rq = make_float3(cl * sm.col_sin[cx], msl, cl * sm.col_cos[cx]);
             const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
             if (!(den < -1e-6f)) {
                 valid = false;
@@ -180,14 +190,8 @@ __device__ float plane_cost(const PixelParams& P, const TileSmem& sm, int lx, in
             const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                if (s < S) {
-                    const SourceView& V = P.src[s];
-                    const float Yx = fmaf(V.R[0], X, fmaf(V.R[1], Y, fmaf(V.R[2], Z, V.t[0])));
-                    const float Yy = fmaf(V.R[3], X, fmaf(V.R[4], Y, fmaf(V.R[5], Z, V.t[1])));
-                    const float Yz = fmaf(V.R[6], X, fmaf(V.R[7], Y, fmaf(V.R[8], Z, V.t[2])));
-                    float uc, vc;
-                    project_dir(Yx, Yy, Yz, V.su, V.ou, V.sv, V.ov, uc, vc);
-                    const float Jc = sample_bilinear(V.tex, V.inv_w, V.inv_h, uc, vc) - c0[s];
+                if (EXACT || s < P.S) {
+                    const float Jc = view_sample(P.src[s], X, Y, Z) - c0[s];
                     const float tw = w * Jc;
                     SJ[s] += tw;
                     SJJ[s] = fmaf(tw, Jc, SJJ[s]);
@@ -202,7 +206,7 @@ __device__ float plane_cost(const PixelParams& P, const TileSmem& sm, int lx, in
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         float c = 3.0f;  // unused slots sort last
-        if (s < S) {
+        if (EXACT || s < P.S) {
             const float varJ = st.Sw * SJJ[s] - SJ[s] * SJ[s];
             const float cov = st.Sw * SIJ[s] - st.SIc * SJ[s];
             if (varJ < eps) {
@@ -240,7 +244,7 @@ __device__ __forceinline__ float3 face_camera(float3 n, float3 rp) {
     return n;
 }
 
-template <int NS, int MODE>
+template <int NS, bool EXACT, int MODE>
 __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_constant__ PixelParams P) {
     __shared__ TileSmem sm;
     const int bx = blockIdx.x * TILE_W, by = blockIdx.y * TILE_H;
@@ -252,7 +256,6 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
     const int x = bx + 2 * tx + ((y + P.colour) & 1);
     if (x >= P.W || y >= P.H) return;
     const int lx = x - bx + P.radius, ly = y - by + P.radius;
-    const size_t N = (size_t)P.W * P.H;
     const size_t i = (size_t)y * P.W + x;
 
     const float3 rp = make_float3(sm.row_cos[ly] * sm.col_sin[lx], -sm.row_sin[ly],
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
 
     if (MODE == MODE_COST) {
         const float3 n = make_float3(P.nx[i], P.ny[i], P.nz[i]);
-        P.cost[i] = plane_cost<NS>(P, sm, lx, ly, st, rp, P.depth[i], n);
+        P.cost[i] = plane_cost<NS, EXACT>(P, sm, lx, ly, st, rp, P.depth[i], n);
         return;
     }
     if (MODE == MODE_INIT) {
@@ -277,51 +280,53 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
         P.nx[i] = n.x;
         P.ny[i] = n.y;
         P.nz[i] = n.z;
-        P.cost[i] = plane_cost<NS>(P, sm, lx, ly, st, rp, d, n);
+        P.cost[i] = plane_cost<NS, EXACT>(P, sm, lx, ly, st, rp, d, n);
         return;
     }
 
-    // MODE_SWEEP: propagation then refinement (Sec. III-C).
+    // MODE_SWEEP: 8 neighbour planes, then n_refine perturbations of the
+    // current best (Sec. III-C); strictly lower cost wins.
     float bd = P.depth[i];
     float3 bn = make_float3(P.nx[i], P.ny[i], P.nz[i]);
     float bc = P.cost[i];
-    (void)N;
-#pragma unroll 1
-    for (int k = 0; k < 8; ++k) {
-        const int qy = y + c_neighbors[P.table][k][1];
-        if (qy < 0 || qy >= P.H) continue;
-        const int qx = wrap_index(x + c_neighbors[P.table][k][0], P.W);
-        const size_t j = (size_t)qy * P.W + qx;
-        const float3 nq = make_float3(P.nx[j], P.ny[j], P.nz[j]);
-        const float den = nq.x * rp.x + nq.y * rp.y + nq.z * rp.z;
-        if (!(den < -1e-6f)) continue;
-        const float3 rq = pixel_bearing(qx, qy, P.W, P.H);
-        const float dc = P.depth[j] * (nq.x * rq.x + nq.y * rq.y + nq.z * rq.z) / den;
-        if (!(dc >= P.d_min && dc <= P.d_max)) continue;
-        const float c = plane_cost<NS>(P, sm, lx, ly, st, rp, dc, nq);
-        if (c < bc) {
-            bc = c;
-            bd = dc;
-            bn = nq;
-        }
-    }
     const float span = P.inv_dmin - P.inv_dmax;
+    const int n_cand = 8 + P.n_refine;
 #pragma unroll 1
-    for (int k = 0; k < P.n_refine; ++k) {
-        const float s = ldexpf(1.0f, -(k + 1));
-        const U4 u = draw_uniform4(i, (uint64_t)P.iter, (uint64_t)(1 + k), P.seed, P.keyframe);
-        float inv = fmaf((2.0f * u.x - 1.0f) * s, span, 1.0f / bd);
-        inv = fminf(P.inv_dmin, fmaxf(P.inv_dmax, inv));
-        const float dc = 1.0f / inv;
-        float3 nc = make_float3(fmaf(s, 2.0f * u.y - 1.0f, bn.x), fmaf(s, 2.0f * u.z - 1.0f, bn.y),
-                                fmaf(s, 2.0f * u.w - 1.0f, bn.z));
-        const float il = 1.0f / sqrtf(nc.x * nc.x + nc.y * nc.y + nc.z * nc.z);
-        nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
-        const float c = plane_cost<NS>(P, sm, lx, ly, st, rp, dc, nc);
-        if (c < bc) {
-            bc = c;
-            bd = dc;
-            bn = nc;
+    for (int k = 0; k < n_cand; ++k) {
+        float dc;
+        float3 nc;
+        bool ok = true;
+        if (k < 8) {
+            const int qy = y + c_neighbors[P.table][k][1];
+            ok = qy >= 0 && qy < P.H;
+            if (ok) {
+                const int qx = wrap_index(x + c_neighbors[P.table][k][0], P.W);
+                const size_t j = (size_t)qy * P.W + qx;
+                nc = make_float3(P.nx[j], P.ny[j], P.nz[j]);
+                const float den = nc.x * rp.x + nc.y * rp.y + nc.z * rp.z;
+                const float3 rq = pixel_bearing(qx, qy, P.W, P.H);
+                dc = P.depth[j] * (nc.x * rq.x + nc.y * rq.y + nc.z * rq.z) / den;
+                ok = den < -1e-6f && dc >= P.d_min && dc <= P.d_max;
+            }
+        } else {
+            const int t = k - 8;
+            const float s = __int_as_float((126 - t) << 23);  // 2^-(t+1)
+            const U4 u = draw_uniform4(i, (uint64_t)P.iter, (uint64_t)(1 + t), P.seed, P.keyframe);
+            float inv = fmaf((2.0f * u.x - 1.0f) * s, span, 1.0f / bd);
+            inv = fminf(P.inv_dmin, fmaxf(P.inv_dmax, inv));
+            dc = 1.0f / inv;
+            nc = make_float3(fmaf(s, 2.0f * u.y - 1.0f, bn.x), fmaf(s, 2.0f * u.z - 1.0f, bn.y),
+                             fmaf(s, 2.0f * u.w - 1.0f, bn.z));
+            const float il = 1.0f / sqrtf(nc.x * nc.x + nc.y * nc.y + nc.z * nc.z);
+            nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
+        }
+        if (ok) {
+            const float c = plane_cost<NS, EXACT>(P, sm, lx, ly, st, rp, dc, nc);
+            if (c < bc) {
+                bc = c;
+                bd = dc;
+                bn = nc;
+            }
         }
     }
     P.depth[i] = bd;
@@ -331,13 +336,13 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
     P.cost[i] = bc;
 }
 
-template <int NS>
+template <int NS, bool EXACT>
 cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t stream) {
     const dim3 grid((p.W + TILE_W - 1) / TILE_W, (p.H + TILE_H - 1) / TILE_H);
     switch (mode) {
-        case MODE_COST: pixel_kernel<NS, MODE_COST><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
-        case MODE_INIT: pixel_kernel<NS, MODE_INIT><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
-        default: pixel_kernel<NS, MODE_SWEEP><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
+        case MODE_COST: pixel_kernel<NS, EXACT, MODE_COST><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
+        case MODE_INIT: pixel_kernel<NS, EXACT, MODE_INIT><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
+        default: pixel_kernel<NS, EXACT, MODE_SWEEP><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
     }
     return cudaGetLastError();
 }

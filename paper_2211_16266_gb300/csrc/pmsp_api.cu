@@ -18,16 +18,25 @@ using namespace pmsp;
 
 namespace pmsp {
 
-template <int NS>
+template <int NS, bool EXACT>
 cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t stream);
 
+// One instantiation per source count 1..10 (views unrolled without guards),
+// a guarded 16-view one above.
 cudaError_t launch_pixel_kernel(const PixelParams& p, int mode, cudaStream_t stream) {
-    if (p.S <= 2) return launch_pixel_kernel_ns<2>(p, mode, stream);
-    if (p.S <= 4) return launch_pixel_kernel_ns<4>(p, mode, stream);
-    if (p.S <= 6) return launch_pixel_kernel_ns<6>(p, mode, stream);
-    if (p.S <= 8) return launch_pixel_kernel_ns<8>(p, mode, stream);
-    if (p.S <= 10) return launch_pixel_kernel_ns<10>(p, mode, stream);
-    return launch_pixel_kernel_ns<16>(p, mode, stream);
+    switch (p.S) {
+        case 1: return launch_pixel_kernel_ns<1, true>(p, mode, stream);
+        case 2: return launch_pixel_kernel_ns<2, true>(p, mode, stream);
+        case 3: return launch_pixel_kernel_ns<3, true>(p, mode, stream);
+        case 4: return launch_pixel_kernel_ns<4, true>(p, mode, stream);
+        case 5: return launch_pixel_kernel_ns<5, true>(p, mode, stream);
+        case 6: return launch_pixel_kernel_ns<6, true>(p, mode, stream);
+        case 7: return launch_pixel_kernel_ns<7, true>(p, mode, stream);
+        case 8: return launch_pixel_kernel_ns<8, true>(p, mode, stream);
+        case 9: return launch_pixel_kernel_ns<9, true>(p, mode, stream);
+        case 10: return launch_pixel_kernel_ns<10, true>(p, mode, stream);
+        default: return launch_pixel_kernel_ns<16, false>(p, mode, stream);
+    }
 }
 
 int ctx_fail(pmsp_ctx* c, int code, const char* fmt, ...) {
@@ -565,6 +574,36 @@ int pmsp_sample_bilinear(pmsp_ctx* c, const pmsp_image* img, int n, const float*
     if (img->memory == PMSP_HOST) {
         e = cudaMemcpyAsync(out, dout, n * 4, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "sample download");
+        return pmsp_sync(c);
+    }
+    return PMSP_OK;
+}
+
+int pmsp_project(pmsp_ctx* c, int W, int H, int n, const float* dirs, float* uc, float* vc, int memory) {
+    if (!c) return PMSP_EINVAL;
+    cudaSetDevice(c->device);
+    if (W < 1 || H < 1 || n < 0 || (n > 0 && (!dirs || !uc || !vc)))
+        return ctx_fail(c, PMSP_EINVAL, "bad projection arguments");
+    if (memory != PMSP_HOST && memory != PMSP_DEVICE) return ctx_fail(c, PMSP_EINVAL, "unknown memory kind");
+    if (n == 0) return PMSP_OK;
+    const float* dd = dirs;
+    float *du = uc, *dv = vc;
+    int rc;
+    if (memory == PMSP_HOST) {
+        if ((rc = ensure_buffer(c, c->sample_stage, 5 * (size_t)n * sizeof(float)))) return rc;
+        float* base = static_cast<float*>(c->sample_stage.ptr);
+        cudaError_t e = cudaMemcpyAsync(base, dirs, 3 * (size_t)n * 4, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "projection upload");
+        dd = base;
+        du = base + 3 * (size_t)n;
+        dv = base + 4 * (size_t)n;
+    }
+    cudaError_t e = launch_project_kernel(W, H, n, dd, du, dv, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "projection launch");
+    if (memory == PMSP_HOST) {
+        e = cudaMemcpyAsync(uc, du, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vc, dv, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "projection download");
         return pmsp_sync(c);
     }
     return PMSP_OK;

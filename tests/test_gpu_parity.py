@@ -156,10 +156,9 @@ def test_one_halfsweep_from_shared_state(pm, ctx, name):
     d, n, c = pb.init()
     # a first sweep on the oracle gives a less trivial shared state
     pb.halfsweep(d, n, c, 0, 0)
-    d = d.astype(np.float32).astype(np.float64)
-    n = n.astype(np.float32).astype(np.float64)
-    c = c.astype(np.float32).astype(np.float64)
     for colour, it in ((1, 0), (0, 1)):
+        # both sides start from the same FP32-representable state
+        d, n, c = (a.astype(np.float32).astype(np.float64) for a in (d, n, c))
         state = _maps_from(pm, d, n, c)
         pm.pmsp_halfsweep(ctx, *_gpu_args(prob), prob.params, colour, it, state)
         gd, gn, gc = (a.cpu().numpy().astype(np.float64) for a in (state.depth, state.normal, state.cost))
@@ -303,3 +302,28 @@ def test_full_size_sampled_parity(pm, ctx):
         ok_c.append(abs(oc - gc[v, u]) <= COST_TOL)
         ok_d.append(abs(od - gd[v, u]) / od <= DEPTH_TOL)
     assert np.mean(ok_c) >= 0.995 and np.mean(ok_d) >= 0.995
+
+
+# ------------------------------------------------------------ projection
+
+def test_projection_matches_fp64(pm, ctx):
+    """Device equirect projection (polynomial arctangent) vs the FP64 oracle."""
+    rng = np.random.default_rng(12)
+    d = rng.normal(size=(20000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d *= rng.uniform(0.2, 12.0, size=(len(d), 1))
+    extra = np.array([[0, 0, 1], [0, 0, -1], [1, 0, 0], [-1, 0, 0], [1e-3, 0, -1], [-1e-3, 0, -1],
+                      [0.3, 0.2, -1e-7], [0.5, -0.5, 0.5]], dtype=float)
+    d = np.concatenate([d, extra])
+    d32 = d.astype(np.float32)
+    for W, H in [(1920, 960), (256, 128), (3840, 1920)]:
+        uc, vc = pm.pmsp_project(ctx, W, H, _dev(d32))
+        uc, vc = uc.cpu().numpy(), vc.cpu().numpy()
+        want = np.array([oracle.project(W, H, x.astype(np.float64)) for x in d32])
+        du = (uc - want[:, 0] + W / 2) % W - W / 2
+        dv = vc - want[:, 1]
+        lat = np.degrees(np.arcsin(np.clip(-d32[:, 1] / np.linalg.norm(d32, axis=1), -1, 1)))
+        ok = np.abs(lat) < 89.5
+        # FP32 coordinates near W carry an ulp of W * 2^-24; the arctangent adds ~1e-7 rad
+        tol = 4e-4 * W / 1920
+        assert np.max(np.abs(du[ok])) < tol and np.max(np.abs(dv)) < tol, (W, np.abs(du[ok]).max(), np.abs(dv).max())
