@@ -206,6 +206,103 @@ int pmsp_sample_bilinear(pmsp_ctx* ctx, const pmsp_image* img, int n, const floa
 int pmsp_project(pmsp_ctx* ctx, int W, int H, int n, const float* dirs, float* uc, float* vc,
                  int memory);
 
+/* ------------------------------------------------------------------------
+ * Batched densification: many keyframes of different sizes and view counts
+ * in one pass. Every phase (initialisation colours, then each half-sweep) is
+ * one persistent launch over the tiles of all keyframes; the per-pixel work
+ * is the single-keyframe computation, so each keyframe's maps equal what
+ * pmsp_densify returns for it alone.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    pmsp_image ref;
+    pmsp_pose ref_pose;
+    const pmsp_image* srcs;     /* n_src source panoramas */
+    const pmsp_pose* src_poses; /* n_src poses */
+    int32_t n_src;
+    pmsp_params params;
+    pmsp_maps out;              /* depth, normal, cost of the reference size */
+} pmsp_batch_item;
+
+/* Launch settings of the batched path (see pmsp_autotune). */
+typedef struct {
+    int32_t blocks_per_sm; /* persistent grid = SMs x blocks_per_sm; 0: the occupancy maximum */
+    int32_t order;         /* work order: 0 largest keyframe first, 1 tiles of all keyframes interleaved */
+    int32_t patch_stride;  /* 0: each item's own stride; > 0: use this stride for every item */
+    int32_t strategy;      /* 0: one persistent launch per phase over all keyframes' tiles;
+                              1: every keyframe's own launch chain, chains run concurrently on
+                                 parallel streams (parallel branches of the captured graph) */
+} pmsp_tuning;
+
+#define PMSP_BATCH_GRAPH 1u /* capture the batch in a CUDA graph and replay it when the identical
+                               batch (same buffers, sizes and parameters) is submitted again;
+                               applies when every buffer is device memory */
+
+/*
+ * Densify n keyframes. tuning may be NULL (defaults). Returns PMSP_EINVAL if
+ * any item is invalid (nothing is run). Device-memory batches return once
+ * enqueued; a batch with host memory returns with the results on the host.
+ */
+int pmsp_densify_batch(pmsp_ctx* ctx, const pmsp_batch_item* items, int n, uint32_t flags,
+                       const pmsp_tuning* tuning);
+
+/*
+ * Pick pmsp_tuning for a batch by timing candidate settings on it (the items'
+ * outputs are overwritten). A coarser patch stride than the items' own is
+ * accepted only if the range it produces stays within 1 % of the items'
+ * own-stride result on at least (1 - max_changed) of the pixels.
+ */
+int pmsp_autotune(pmsp_ctx* ctx, const pmsp_batch_item* items, int n, float max_changed,
+                  pmsp_tuning* out);
+
+/* ------------------------------------------------------------------------
+ * Serving (the densification thread of Sec. III: keyframes arrive from the
+ * SLAM front end, each is densified against a small neighbourhood of
+ * keyframes, filtered against neighbouring depth maps and handed on).
+ * Frames live in a device ring of the last ring_capacity pushes; requests
+ * are admitted while a slot is free (max_active) and their maps fit under
+ * mem_cap_bytes, and every scheduler step advances every admitted request by
+ * one phase in one persistent launch (iteration-level continuous batching).
+ * A request's maps do not depend on which other requests share its launches.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int64_t ref_frame;            /* reference frame id (in the ring) */
+    int32_t n_src;
+    const int64_t* src_frames;    /* n_src source frame ids */
+    pmsp_params params;
+    int32_t n_filter;             /* 0: no filter; else neighbour frame ids whose depth maps */
+    const int64_t* filter_frames; /*    (from finished requests) filter this result */
+    float max_reproj_px;          /* filter threshold (pixels) */
+    int32_t min_views;            /* filter: views that must agree */
+} pmsp_request;
+
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    uint32_t queued, active;
+    uint64_t steps;               /* scheduler launches so far */
+    uint64_t bytes_in_use;        /* maps of admitted and unretrieved requests */
+} pmsp_serving_stats;
+
+/* Copy a frame into the ring (evicting the oldest frame no queued or active
+ * request uses). Re-pushing an id replaces it. PMSP_EBUSY: every slot is in use. */
+int pmsp_ring_push(pmsp_ctx* ctx, int64_t frame_id, const pmsp_image* img, const pmsp_pose* pose);
+
+/* Queue a request; *ticket identifies it. PMSP_ENOTFOUND: a frame id is not in
+ * the ring; PMSP_EADMIT: its maps alone exceed mem_cap_bytes; PMSP_EINVAL: bad
+ * parameters. Returns without waiting for the GPU. */
+int pmsp_submit(pmsp_ctx* ctx, const pmsp_request* req, uint64_t* ticket);
+
+/* PMSP_OK once the request has finished: its maps (depth after the filter,
+ * normal, cost; the reference frame's size) are copied into *out (NULL:
+ * discarded) and the ticket is released. PMSP_EBUSY while it is queued or
+ * running; PMSP_ENOTFOUND for an unknown or released ticket. */
+int pmsp_poll(pmsp_ctx* ctx, uint64_t ticket, pmsp_maps* out);
+
+/* pmsp_poll, blocking up to timeout_ms (PMSP_ETIMEDOUT when it expires). */
+int pmsp_wait(pmsp_ctx* ctx, uint64_t ticket, int timeout_ms, pmsp_maps* out);
+
+/* Counters of the serving runtime. */
+int pmsp_get_serving_stats(pmsp_ctx* ctx, pmsp_serving_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

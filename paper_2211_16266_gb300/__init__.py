@@ -18,7 +18,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpmsp.so")
+LIB_PATH = os.environ.get("PMSP_LIB") or os.path.join(_HERE, "libpmsp.so")  # PMSP_LIB: another build
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libpmsp.so is missing at {LIB_PATH}: build the CUDA library first "
@@ -99,6 +99,24 @@ _SIGS = {
     "pmsp_sample_bilinear": ([_P, _I, ctypes.c_int, _F, _F, _F], ctypes.c_int),
     "pmsp_project": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _F, _F, _F, ctypes.c_int], ctypes.c_int),
 }
+
+
+class pmsp_batch_item(ctypes.Structure):
+    _fields_ = [("ref", pmsp_image), ("ref_pose", pmsp_pose), ("srcs", ctypes.POINTER(pmsp_image)),
+                ("src_poses", ctypes.POINTER(pmsp_pose)), ("n_src", ctypes.c_int32), ("params", pmsp_params),
+                ("out", pmsp_maps)]
+
+
+class pmsp_tuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("order", ctypes.c_int32), ("patch_stride", ctypes.c_int32),
+                ("strategy", ctypes.c_int32)]
+
+
+PMSP_BATCH_GRAPH = 1
+_SIGS["pmsp_densify_batch"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int, ctypes.c_uint32,
+                                ctypes.POINTER(pmsp_tuning)], ctypes.c_int)
+_SIGS["pmsp_autotune"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int, ctypes.c_float,
+                           ctypes.POINTER(pmsp_tuning)], ctypes.c_int)
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.argtypes = _args
@@ -208,9 +226,15 @@ def _ptr(a):
 
 
 class Context:
-    """Owns a pmsp_ctx. stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    """Owns a pmsp_ctx. stream: "torch" (default: torch's current stream), a torch.cuda.Stream,
+    a raw cudaStream_t int, or None (the context creates its own stream)."""
 
-    def __init__(self, device=0, stream=None, mem_cap_bytes=0, ring_capacity=0, max_active=0):
+    def __init__(self, device=0, stream="torch", mem_cap_bytes=0, ring_capacity=0, max_active=0):
+        # default: torch's current stream on `device`, so work is ordered after the
+        # torch copies that produce the inputs; None: a private stream
+        if isinstance(stream, str) and stream == "torch":
+            import torch
+            stream = torch.cuda.current_stream(device)
         raw = None
         if stream is not None:
             raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
@@ -246,7 +270,7 @@ class Context:
         self.close()
 
 
-def pmsp_create(device=0, stream=None, **kw):
+def pmsp_create(device=0, stream="torch", **kw):
     return Context(device, stream, **kw)
 
 
@@ -374,3 +398,108 @@ def pmsp_project(ctx, W, H, dirs):
         mem = PMSP_HOST
     ctx.check(_lib.pmsp_project(ctx.h, int(W), int(H), int(d.shape[0]), _ptr(d), _ptr(uc), _ptr(vc), mem))
     return uc, vc
+
+
+class Batch:
+    """Marshalled pmsp_batch_item array; keeps every referenced buffer alive.
+
+    problems: iterable of (ref, ref_pose, srcs, src_poses, params, out) where
+    out is a Maps or None (allocated like pmsp_densify's output).
+    """
+
+    def __init__(self, problems):
+        self.keep = []
+        self.outs = []
+        probs = list(problems)
+        self.items = (pmsp_batch_item * len(probs))()
+        for k, (ref, ref_pose, srcs, src_poses, params, out) in enumerate(probs):
+            cref, rp, cs, cp, n, p = _problem(ref, ref_pose, srcs, src_poses, params, self.keep)
+            out = _out_maps(ref, out)
+            self.outs.append(out)
+            it = self.items[k]
+            it.ref, it.ref_pose, it.n_src, it.params, it.out = cref, rp, n, p, out.c()
+            it.srcs = ctypes.cast(cs, ctypes.POINTER(pmsp_image))
+            it.src_poses = ctypes.cast(cp, ctypes.POINTER(pmsp_pose))
+
+    def __len__(self):
+        return len(self.outs)
+
+
+def pmsp_densify_batch(ctx, batch, flags=0, tuning=None):
+    """Densify every problem of a Batch; returns the list of output Maps."""
+    t = ctypes.byref(tuning) if tuning is not None else None
+    ctx.check(_lib.pmsp_densify_batch(ctx.h, batch.items, len(batch), int(flags), t))
+    return batch.outs
+
+
+def pmsp_autotune(ctx, batch, max_changed=0.005):
+    t = pmsp_tuning()
+    ctx.check(_lib.pmsp_autotune(ctx.h, batch.items, len(batch), float(max_changed), ctypes.byref(t)))
+    return t
+
+
+# ------------------------------------------------------------------- serving
+
+class pmsp_request(ctypes.Structure):
+    _fields_ = [("ref_frame", ctypes.c_int64), ("n_src", ctypes.c_int32),
+                ("src_frames", ctypes.POINTER(ctypes.c_int64)), ("params", pmsp_params),
+                ("n_filter", ctypes.c_int32), ("filter_frames", ctypes.POINTER(ctypes.c_int64)),
+                ("max_reproj_px", ctypes.c_float), ("min_views", ctypes.c_int32)]
+
+
+class pmsp_serving_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("queued", ctypes.c_uint32), ("active", ctypes.c_uint32), ("steps", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_uint64)]
+
+
+for _name, _args in {
+    "pmsp_ring_push": [_P, ctypes.c_int64, _I, _O],
+    "pmsp_submit": [_P, ctypes.POINTER(pmsp_request), ctypes.POINTER(ctypes.c_uint64)],
+    "pmsp_poll": [_P, ctypes.c_uint64, _M],
+    "pmsp_wait": [_P, ctypes.c_uint64, ctypes.c_int, _M],
+    "pmsp_get_serving_stats": [_P, ctypes.POINTER(pmsp_serving_stats)],
+}.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_int
+C_SYMBOLS = C_SYMBOLS + ("pmsp_ring_push", "pmsp_submit", "pmsp_poll", "pmsp_wait", "pmsp_get_serving_stats")
+
+
+def pmsp_ring_push(ctx, frame_id, image, pose):
+    keep = []
+    im = make_image(image, keep)
+    ctx.check(_lib.pmsp_ring_push(ctx.h, int(frame_id), ctypes.byref(im), ctypes.byref(make_pose(pose))))
+
+
+def pmsp_submit(ctx, ref_frame, src_frames, params=None, filter_frames=(), max_reproj_px=1.0, min_views=2):
+    """Queue a densification request; returns its ticket."""
+    srcs = (ctypes.c_int64 * len(src_frames))(*[int(f) for f in src_frames])
+    filt = (ctypes.c_int64 * max(1, len(filter_frames)))(*[int(f) for f in filter_frames])
+    req = pmsp_request(int(ref_frame), len(src_frames), srcs, make_params(params), len(filter_frames), filt,
+                       float(max_reproj_px), int(min_views))
+    t = ctypes.c_uint64()
+    ctx.check(_lib.pmsp_submit(ctx.h, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def pmsp_poll(ctx, ticket, out=None):
+    """Maps if finished (copied into `out`), None while queued or running."""
+    m = out.c() if out is not None else None
+    rc = _lib.pmsp_poll(ctx.h, int(ticket), ctypes.byref(m) if m is not None else None)
+    if rc == PMSP_EBUSY:
+        return None
+    ctx.check(rc)
+    return out
+
+
+def pmsp_wait(ctx, ticket, timeout_ms, out=None):
+    m = out.c() if out is not None else None
+    ctx.check(_lib.pmsp_wait(ctx.h, int(ticket), int(timeout_ms), ctypes.byref(m) if m is not None else None))
+    return out
+
+
+def pmsp_get_serving_stats(ctx):
+    s = pmsp_serving_stats()
+    ctx.check(_lib.pmsp_get_serving_stats(ctx.h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_}

@@ -20,18 +20,18 @@ constexpr int MAX_HALO = (PMSP_MAX_PATCH_W - 1) / 2;
 constexpr unsigned ERR_BAD_INDEX = 1u;
 
 // One source view as the kernels see it.
-struct SourceView {
-    cudaTextureObject_t tex;  // gather-capable texture: x wraps, y clamps, normalised coords
-    float R[9];               // reference camera -> source camera rotation, row-major
-    float t[3];
-    float su, ou;             // u_c = lon * su + ou
-    float sv, ov;             // v_c = lat * sv + ov
+// m[0..11]: rows of the reference->source rigid transform with the
+// translation last (Y_i = m[4i..4i+2] . X + m[4i+3]); m[12..15]: (su, ou, sv, ov)
+// with u_c = lon * su + ou, v_c = lat * sv + ov.
+struct alignas(16) SourceView {
+    float m[16];
     float inv_w, inv_h;       // 1/W, 1/H of this source
+    cudaTextureObject_t tex;  // gather-capable texture: x wraps, y clamps, normalised coords
 };
 
 enum Mode : int { MODE_COST = 0, MODE_INIT = 1, MODE_SWEEP = 2 };
 
-struct PixelParams {
+struct alignas(16) PixelParams {
     SourceView src[PMSP_MAX_SOURCES];
     const uint8_t* ref;   // reference image, linear, row pitch ref_pitch bytes
     int64_t ref_pitch;
@@ -54,6 +54,7 @@ struct PixelParams {
     float wc;             // -log2(e) / (2 sigma_c^2), 0 when off
     float ws;             // -log2(e) / (2 sigma_s^2), 0 when off
     unsigned long long seed, keyframe;
+    int phase;            // batched serving: 0,1 initialisation colours, 2 + 2 t + c half-sweep (t, c)
     int colour;
     int iter;
     unsigned* err;
@@ -75,7 +76,21 @@ struct FilterParams {
     float max_px;
 };
 
-// Launchers (one translation unit per source-count bucket).
+// Arguments of one launch of the persistent batched kernel.
+struct BatchArgs {
+    const PixelParams* problems;  // device array, one per keyframe
+    const int4* work;             // (problem, tile x0, tile y0, phase) items
+    int n_work;
+    int phase;                    // >= 0: phase of every item; -1: each item's own; -2: each problem's own
+    unsigned* counter;            // work-item counter, zero before the launch
+};
+
+// Launchers. The batched kernel comes in instances for at most
+// MAXS in {4, 6, 8, 10, 16} views (batch_s<MAXS>.cu).
+template <int MAXS>
+int batch_kernel_blocks_per_sm_t();
+template <int MAXS>
+cudaError_t launch_batch_kernel_t(const BatchArgs& a, int grid, cudaStream_t stream);
 cudaError_t launch_pixel_kernel(const PixelParams& p, int mode, cudaStream_t stream);
 cudaError_t launch_filter_kernel(const FilterParams& p, cudaStream_t stream);
 cudaError_t launch_project_kernel(int W, int H, int n, const float* dirs, float* uc, float* vc,

@@ -37,6 +37,10 @@ constexpr int TILE_PITCH = TILE_W + 2 * MAX_HALO;
 constexpr int TILE_ROWS = TILE_H + 2 * MAX_HALO;
 constexpr int MAX_K = 2 * MAX_HALO + 1;
 
+// Resident blocks per SM the register budget is sized for, by view count:
+// the per-view sums grow with the views (64 to 96 registers per thread).
+constexpr int min_blocks_for(int ns) { return ns <= 4 ? 8 : ns <= 6 ? 7 : ns <= 8 ? 6 : ns <= 10 ? 5 : 4; }
+
 struct TileSmem {
     float ref[TILE_ROWS * TILE_PITCH];  // normalised intensities, halo included
     float row_cos[TILE_ROWS], row_sin[TILE_ROWS];    // cos lat, sin lat
@@ -129,20 +133,74 @@ __device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const TileSm
     return st;
 }
 
+// Where the per-view constants are read from. Kernel parameters: plain member
+// reads (they become constant-bank operands). Shared memory (the batched
+// kernel): volatile vector loads at every use, so the compiler reloads them
+// instead of holding all views' constants in registers.
+struct ParamViews {
+    // Reads go straight to the parameter at each use, so they stay
+    // constant-bank operands of the arithmetic instead of register copies.
+    struct Loaded {
+        const SourceView& V;
+        __device__ __forceinline__ float m(int k) const { return V.m[k]; }
+        __device__ __forceinline__ float inv_w() const { return V.inv_w; }
+        __device__ __forceinline__ float inv_h() const { return V.inv_h; }
+        __device__ __forceinline__ cudaTextureObject_t tex() const { return V.tex; }
+    };
+    __device__ __forceinline__ static Loaded load(const SourceView& V) { return Loaded{V}; }
+};
+
+struct SharedViews {
+    __device__ __forceinline__ static float4 ld4(const float4* p) {
+        float4 v;
+        const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+        return v;
+    }
+    struct Loaded {
+        float v[16];
+        float iw, ih;
+        cudaTextureObject_t t;
+        __device__ __forceinline__ float m(int k) const { return v[k]; }
+        __device__ __forceinline__ float inv_w() const { return iw; }
+        __device__ __forceinline__ float inv_h() const { return ih; }
+        __device__ __forceinline__ cudaTextureObject_t tex() const { return t; }
+    };
+    __device__ __forceinline__ static Loaded load(const SourceView& V) {
+        Loaded L;
+        const float4* q = reinterpret_cast<const float4*>(V.m);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 a = ld4(q + k);
+            L.v[4 * k] = a.x;
+            L.v[4 * k + 1] = a.y;
+            L.v[4 * k + 2] = a.z;
+            L.v[4 * k + 3] = a.w;
+        }
+        const float4 b = ld4(reinterpret_cast<const float4*>(&V.inv_w));
+        L.iw = b.x;
+        L.ih = b.y;
+        L.t = (cudaTextureObject_t)(((unsigned long long)__float_as_uint(b.w) << 32) | __float_as_uint(b.z));
+        return L;
+    }
+};
+
 // Intensity of source view V at the projection of reference-frame point X.
+template <class VA>
 __device__ __forceinline__ float view_sample(const SourceView& V, float X, float Y, float Z) {
-    const float Yx = fmaf(V.R[0], X, fmaf(V.R[1], Y, fmaf(V.R[2], Z, V.t[0])));
-    const float Yy = fmaf(V.R[3], X, fmaf(V.R[4], Y, fmaf(V.R[5], Z, V.t[1])));
-    const float Yz = fmaf(V.R[6], X, fmaf(V.R[7], Y, fmaf(V.R[8], Z, V.t[2])));
+    const typename VA::Loaded L = VA::load(V);
+    const float Yx = fmaf(L.m(0), X, fmaf(L.m(1), Y, fmaf(L.m(2), Z, L.m(3))));
+    const float Yy = fmaf(L.m(4), X, fmaf(L.m(5), Y, fmaf(L.m(6), Z, L.m(7))));
+    const float Yz = fmaf(L.m(8), X, fmaf(L.m(9), Y, fmaf(L.m(10), Z, L.m(11))));
     float uc, vc;
-    project_dir_fast(Yx, Yy, Yz, V.su, V.ou, V.sv, V.ov, uc, vc);
-    return sample_bilinear(V.tex, V.inv_w, V.inv_h, uc, vc);
+    project_dir_fast(Yx, Yy, Yz, L.m(12), L.m(13), L.m(14), L.m(15), uc, vc);
+    return sample_bilinear(L.tex(), L.inv_w(), L.inv_h(), uc, vc);
 }
 
 // Cost of plane (range d along rp, unit normal n) at the pixel. Returns 2 for
 // an invalid plane (a patch ray meets it from behind or grazing). NS views
 // are kept in registers; EXACT means S == NS (no per-view guard).
-template <int NS, bool EXACT>
+template <int NS, bool EXACT, class VA>
 __device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem& sm, int lx, int ly,
                                             const RefStats& st, float3 rp, float d, float3 n) {
     const float eps = 1e-8f * st.Sw * st.Sw;
@@ -166,7 +224,7 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem
             SJ[s] = 0.f;
             SJJ[s] = 0.f;
             SIJ[s] = 0.f;
-            if (EXACT || s < P.S) c0[s] = view_sample(P.src[s], X, Y, Z);
+            if (EXACT || s < P.S) c0[s] = view_sample<VA>(P.src[s], X, Y, Z);
         }
     }
     bool valid = true;
@@ -191,7 +249,7 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 if (EXACT || s < P.S) {
-                    const float Jc = view_sample(P.src[s], X, Y, Z) - c0[s];
+                    const float Jc = view_sample<VA>(P.src[s], X, Y, Z) - c0[s];
                     const float tw = w * Jc;
                     SJ[s] += tw;
                     SJJ[s] = fmaf(tw, Jc, SJJ[s]);
@@ -244,16 +302,18 @@ __device__ __forceinline__ float3 face_camera(float3 n, float3 rp) {
     return n;
 }
 
-template <int NS, bool EXACT, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_constant__ PixelParams P) {
-    __shared__ TileSmem sm;
-    const int bx = blockIdx.x * TILE_W, by = blockIdx.y * TILE_H;
+// One tile of one problem: stage the reference tile, then every active
+// pixel of `colour` runs MODE. P may live in kernel parameters or in shared
+// memory (the batched kernel). Returns without a trailing barrier.
+template <int NS, bool EXACT, int MODE, class VA = ParamViews>
+__device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm, int bx, int by, int colour,
+                                             int iter) {
     stage_tile(P, sm, bx, by);
     __syncthreads();
 
     const int tx = threadIdx.x % (TILE_W / 2), ty = threadIdx.x / (TILE_W / 2);
     const int y = by + ty;
-    const int x = bx + 2 * tx + ((y + P.colour) & 1);
+    const int x = bx + 2 * tx + ((y + colour) & 1);
     if (x >= P.W || y >= P.H) return;
     const int lx = x - bx + P.radius, ly = y - by + P.radius;
     const size_t i = (size_t)y * P.W + x;
@@ -264,7 +324,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
 
     if (MODE == MODE_COST) {
         const float3 n = make_float3(P.nx[i], P.ny[i], P.nz[i]);
-        P.cost[i] = plane_cost<NS, EXACT>(P, sm, lx, ly, st, rp, P.depth[i], n);
+        P.cost[i] = plane_cost<NS, EXACT, VA>(P, sm, lx, ly, st, rp, P.depth[i], n);
         return;
     }
     if (MODE == MODE_INIT) {
@@ -280,7 +340,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
         P.nx[i] = n.x;
         P.ny[i] = n.y;
         P.nz[i] = n.z;
-        P.cost[i] = plane_cost<NS, EXACT>(P, sm, lx, ly, st, rp, d, n);
+        P.cost[i] = plane_cost<NS, EXACT, VA>(P, sm, lx, ly, st, rp, d, n);
         return;
     }
 
@@ -311,7 +371,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
         } else {
             const int t = k - 8;
             const float s = __int_as_float((126 - t) << 23);  // 2^-(t+1)
-            const U4 u = draw_uniform4(i, (uint64_t)P.iter, (uint64_t)(1 + t), P.seed, P.keyframe);
+            const U4 u = draw_uniform4(i, (uint64_t)iter, (uint64_t)(1 + t), P.seed, P.keyframe);
             float inv = fmaf((2.0f * u.x - 1.0f) * s, span, 1.0f / bd);
             inv = fminf(P.inv_dmin, fmaxf(P.inv_dmax, inv));
             dc = 1.0f / inv;
@@ -321,7 +381,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
             nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
         }
         if (ok) {
-            const float c = plane_cost<NS, EXACT>(P, sm, lx, ly, st, rp, dc, nc);
+            const float c = plane_cost<NS, EXACT, VA>(P, sm, lx, ly, st, rp, dc, nc);
             if (c < bc) {
                 bc = c;
                 bd = dc;
@@ -334,6 +394,12 @@ __global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_const
     P.ny[i] = bn.y;
     P.nz[i] = bn.z;
     P.cost[i] = bc;
+}
+
+template <int NS, bool EXACT, int MODE>
+__global__ void __launch_bounds__(BLOCK_THREADS, min_blocks_for(NS)) pixel_kernel(const __grid_constant__ PixelParams P) {
+    __shared__ TileSmem sm;
+    process_tile<NS, EXACT, MODE>(P, sm, blockIdx.x * TILE_W, blockIdx.y * TILE_H, P.colour, P.iter);
 }
 
 template <int NS, bool EXACT>

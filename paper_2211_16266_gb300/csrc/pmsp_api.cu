@@ -200,36 +200,53 @@ int prepare_problem(pmsp_ctx* c, const pmsp_image* ref, const pmsp_pose* ref_pos
     for (int s = 0; s < n_src; ++s)
         if ((rc = check_image(c, &srcs[s], "source"))) return rc;
 
-    memset(&P, 0, sizeof P);
     if ((int)c->src_tex.size() < n_src) c->src_tex.resize(n_src);
+    cudaTextureObject_t tex[PMSP_MAX_SOURCES];
     for (int s = 0; s < n_src; ++s) {
         if ((rc = upload_texture(c, c->src_tex[s], &srcs[s]))) return rc;
-        double R[9], t[3];
-        compose_rel(*ref_pose, src_poses[s], R, t);
-        SourceView& V = P.src[s];
-        V.tex = c->src_tex[s].tex;
-        for (int k = 0; k < 9; ++k) V.R[k] = (float)R[k];
-        for (int k = 0; k < 3; ++k) V.t[k] = (float)t[k];
-        const double Ws = srcs[s].w, Hs = srcs[s].h;
-        V.su = (float)(Ws / (2.0 * M_PI));
-        V.ou = (float)(0.5 * Ws - 0.5);
-        V.sv = (float)(-Hs / M_PI);
-        V.ov = (float)(0.5 * Hs - 0.5);
-        V.inv_w = (float)(1.0 / Ws);
-        V.inv_h = (float)(1.0 / Hs);
+        tex[s] = c->src_tex[s].tex;
     }
-    if (ref->memory == PMSP_DEVICE) {
-        P.ref = static_cast<const uint8_t*>(ref->data);
-        P.ref_pitch = ref->pitch_bytes;
-    } else {
+    const void* ref_dev = ref->data;
+    int64_t ref_pitch = ref->pitch_bytes;
+    if (ref->memory != PMSP_DEVICE) {
         const size_t row = (size_t)ref->w * format_bytes(ref->format);
         if ((rc = ensure_buffer(c, c->ref_stage, row * ref->h))) return rc;
         cudaError_t e = cudaMemcpy2DAsync(c->ref_stage.ptr, row, ref->data, ref->pitch_bytes, row, ref->h,
                                           cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "reference upload");
-        P.ref = static_cast<const uint8_t*>(c->ref_stage.ptr);
-        P.ref_pitch = (int64_t)row;
+        ref_dev = c->ref_stage.ptr;
+        ref_pitch = (int64_t)row;
     }
+    fill_problem(P, ref, ref_dev, ref_pitch, ref_pose, srcs, tex, src_poses, n_src, p);
+    P.err = c->d_err;
+    return PMSP_OK;
+}
+
+// Kernel parameters of one problem from validated arguments: FP64 pose
+// composition cast to FP32, projection scales, window and weight constants.
+void fill_problem(PixelParams& P, const pmsp_image* ref, const void* ref_dev, int64_t ref_pitch,
+                  const pmsp_pose* ref_pose, const pmsp_image* srcs, const cudaTextureObject_t* tex,
+                  const pmsp_pose* src_poses, int n_src, const pmsp_params* p) {
+    memset(&P, 0, sizeof P);
+    for (int s = 0; s < n_src; ++s) {
+        double R[9], t[3];
+        compose_rel(*ref_pose, src_poses[s], R, t);
+        SourceView& V = P.src[s];
+        V.tex = tex[s];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) V.m[4 * i + j] = (float)R[3 * i + j];
+            V.m[4 * i + 3] = (float)t[i];
+        }
+        const double Ws = srcs[s].w, Hs = srcs[s].h;
+        V.m[12] = (float)(Ws / (2.0 * M_PI));
+        V.m[13] = (float)(0.5 * Ws - 0.5);
+        V.m[14] = (float)(-Hs / M_PI);
+        V.m[15] = (float)(0.5 * Hs - 0.5);
+        V.inv_w = (float)(1.0 / Ws);
+        V.inv_h = (float)(1.0 / Hs);
+    }
+    P.ref = static_cast<const uint8_t*>(ref_dev);
+    P.ref_pitch = ref_pitch;
     P.ref_format = ref->format;
     P.W = ref->w;
     P.H = ref->h;
@@ -249,8 +266,6 @@ int prepare_problem(pmsp_ctx* c, const pmsp_image* ref, const pmsp_pose* ref_pos
     P.ws = p->sigma_space > 0 ? (float)(-log2e / (2.0 * (double)p->sigma_space * p->sigma_space)) : 0.f;
     P.seed = p->seed;
     P.keyframe = p->keyframe_id;
-    P.err = c->d_err;
-    return PMSP_OK;
 }
 
 // Bind state planes: device maps directly, host maps through staging.
@@ -297,8 +312,6 @@ int finish_maps(pmsp_ctx* c, pmsp_maps* m, const PixelParams& P, bool depth_norm
     if (e != cudaSuccess) return cuda_fail(c, e, "map download");
     return pmsp_sync(c);
 }
-
-void runtime_shutdown(pmsp_ctx*) {}
 
 int launch(pmsp_ctx* c, const PixelParams& P, int mode) {
     cudaError_t e = launch_pixel_kernel(P, mode, c->stream);

@@ -24,9 +24,28 @@ struct TexImage {
 
 struct Serving;  // continuous-batching runtime (serving calls)
 
+struct PixelParams;
+struct BatchEngine;
+
 int ctx_fail(pmsp_ctx* c, int code, const char* fmt, ...);
 int cuda_fail(pmsp_ctx* c, cudaError_t e, const char* what);
 void runtime_shutdown(pmsp_ctx* c);
+size_t format_bytes(int fmt);
+int check_image(pmsp_ctx* c, const pmsp_image* im, const char* what);
+int check_params(pmsp_ctx* c, const pmsp_params* p, int n_src);
+int check_maps(pmsp_ctx* c, const pmsp_maps* m, int W, int H, bool need_normal, bool need_cost, const char* what);
+int ensure_buffer(pmsp_ctx* c, DevBuffer& b, size_t bytes);
+int upload_texture(pmsp_ctx* c, TexImage& t, const pmsp_image* im);
+void free_texture(TexImage& t);
+void compose_rel(const pmsp_pose& r, const pmsp_pose& s, double R[9], double t[3]);
+void fill_problem(PixelParams& P, const pmsp_image* ref, const void* ref_dev, int64_t ref_pitch,
+                  const pmsp_pose* ref_pose, const pmsp_image* srcs, const cudaTextureObject_t* tex,
+                  const pmsp_pose* src_poses, int n_src, const pmsp_params* p);
+void batch_shutdown(pmsp_ctx* c);
+struct BatchArgs;
+int batch_bucket(int max_s);
+int batch_blocks_per_sm(int bucket);
+cudaError_t batch_launch(int bucket, const BatchArgs& a, int grid, cudaStream_t st);
 
 }  // namespace pmsp
 
@@ -43,4 +62,5 @@ struct pmsp_ctx {
     pmsp::TexImage sample_tex;
     pmsp::DevBuffer ref_stage, map_stage, filter_stage, sample_stage;
     pmsp::Serving* serving = nullptr;
+    pmsp::BatchEngine* batch = nullptr;
 };

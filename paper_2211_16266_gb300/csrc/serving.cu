@@ -1,0 +1,576 @@
+// Serving runtime: device frame ring, admission by slots and memory, and a
+// scheduler thread that advances every admitted request by one phase per
+// launch of the persistent batched kernel (iteration-level continuous
+// batching). Paper Sec. III runs densification in its own thread fed by a
+// keyframe queue; this is that thread, reshaped for many concurrent
+// keyframes on one GPU.
+//
+// Host waits are bounded: the scheduler polls CUDA events with a deadline
+// and fails the in-flight requests with PMSP_ETIMEDOUT instead of blocking;
+// pmsp_wait blocks on a condition variable up to the caller's timeout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "pmsp.h"
+#include "runtime.h"
+
+namespace pmsp {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct RingFrame {
+    int64_t id = -1;
+    bool used = false;
+    uint64_t seq = 0;      // push order, for eviction
+    int pins = 0;          // queued or active requests using the frame
+    int w = 0, h = 0, fmt = 0;
+    pmsp_pose pose{};
+    TexImage tex;          // as a source
+    DevBuffer lin;         // as a reference (row-major, unpadded)
+    DevBuffer depth;       // depth of the last finished request with this reference
+    bool has_depth = false;
+};
+
+enum Status { QUEUED, ACTIVE, FINISHING, DONE, FAILED };
+
+struct Request {
+    uint64_t ticket = 0;
+    int status = QUEUED;
+    int fail_code = PMSP_OK;
+    int ref = -1;
+    std::vector<int> srcs, filters;
+    pmsp_params params{};
+    float max_px = 1.f;
+    int min_views = 2;
+    int W = 0, H = 0;
+    int phase = 0, n_phases = 0;
+    size_t bytes = 0;
+    DevBuffer maps;        // depth, nx, ny, nz, cost, filtered depth
+    cudaEvent_t done = nullptr;
+    PixelParams prob;
+};
+
+}  // namespace
+
+struct Serving {
+    pmsp_ctx* ctx = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread th;
+    bool stop = false;
+    cudaStream_t stream = nullptr;
+    std::vector<RingFrame> ring;
+    uint64_t push_seq = 0;
+    std::deque<Request*> queue;
+    std::vector<Request*> active, finishing;
+    std::map<uint64_t, Request*> tickets;
+    uint64_t next_ticket = 1;
+    uint64_t bytes_in_use = 0;
+    pmsp_serving_stats stats{};
+    // scheduler buffers (one pinned staging slot per in-flight step)
+    DevBuffer d_problems, d_work, d_counter;
+    void* h_problems[2] = {nullptr, nullptr};
+    void* h_work[2] = {nullptr, nullptr};
+    size_t h_problems_bytes[2] = {0, 0}, h_work_bytes[2] = {0, 0};
+    cudaEvent_t slot_ev[2] = {nullptr, nullptr};
+    bool slot_busy[2] = {false, false};
+    int sms = 0;
+    std::string err;
+};
+
+namespace {
+
+constexpr double STEP_DEADLINE_S = 60.0;
+
+int find_frame(Serving& s, int64_t id) {
+    for (int i = 0; i < (int)s.ring.size(); ++i)
+        if (s.ring[i].used && s.ring[i].id == id) return i;
+    return -1;
+}
+
+// Poll an event until it completes or the deadline passes (no unbounded wait).
+bool wait_event(cudaEvent_t ev, double seconds) {
+    const auto until = Clock::now() + std::chrono::duration<double>(seconds);
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return true;
+        if (e != cudaErrorNotReady) return false;
+        if (Clock::now() > until) return false;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+int ensure_host(void*& p, size_t& have, size_t need) {
+    if (have >= need) return PMSP_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    have = 0;
+    if (cudaMallocHost(&p, need) != cudaSuccess) return PMSP_ENOMEM;
+    have = need;
+    return PMSP_OK;
+}
+
+int dev_alloc(DevBuffer& b, size_t bytes) {
+    if (b.bytes >= bytes) return PMSP_OK;
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) return PMSP_ENOMEM;
+    b.bytes = bytes;
+    return PMSP_OK;
+}
+
+// Give back a request's frames and maps (stream-ordered free: no device-wide sync).
+void release_request(Serving& s, Request* r) {
+    for (int f : r->srcs) s.ring[f].pins--;
+    for (int f : r->filters) s.ring[f].pins--;
+    s.ring[r->ref].pins--;
+    if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, s.stream);
+    if (r->done) cudaEventDestroy(r->done);
+    if (r->status == ACTIVE || r->status == FINISHING || r->status == DONE) s.bytes_in_use -= r->bytes;
+    delete r;
+}
+
+// Build one request's kernel parameters; called at admission (maps allocated).
+void fill_request(Serving& s, Request* r) {
+    RingFrame& ref = s.ring[r->ref];
+    pmsp_image ri{ref.w, ref.h, (int64_t)ref.w * (int64_t)format_bytes(ref.fmt), ref.fmt, PMSP_DEVICE, ref.lin.ptr};
+    pmsp_image si[PMSP_MAX_SOURCES];
+    pmsp_pose sp[PMSP_MAX_SOURCES];
+    cudaTextureObject_t tex[PMSP_MAX_SOURCES];
+    for (size_t k = 0; k < r->srcs.size(); ++k) {
+        const RingFrame& f = s.ring[r->srcs[k]];
+        si[k] = pmsp_image{f.w, f.h, (int64_t)f.w * (int64_t)format_bytes(f.fmt), f.fmt, PMSP_DEVICE, f.lin.ptr};
+        sp[k] = f.pose;
+        tex[k] = f.tex.tex;
+    }
+    fill_problem(r->prob, &ri, ref.lin.ptr, ri.pitch_bytes, &ref.pose, si, tex, sp, (int)r->srcs.size(), &r->params);
+    const size_t N = (size_t)r->W * r->H;
+    float* base = static_cast<float*>(r->maps.ptr);
+    r->prob.depth = base;
+    r->prob.nx = base + N;
+    r->prob.ny = base + 2 * N;
+    r->prob.nz = base + 3 * N;
+    r->prob.cost = base + 4 * N;
+    r->prob.err = s.ctx->d_err;
+}
+
+void fail_all(Serving& s, std::vector<Request*>& v, int code) {
+    for (Request* r : v) {
+        r->status = FAILED;
+        r->fail_code = code;
+    }
+    v.clear();
+}
+
+// The finishing step of a request: consistency filter against the depth maps
+// of the named neighbours that exist, then remember this depth in the ring.
+int enqueue_finish(Serving& s, Request* r) {
+    const size_t N = (size_t)r->W * r->H;
+    float* base = static_cast<float*>(r->maps.ptr);
+    float* filtered = base + 5 * N;
+    FilterParams F;
+    memset(&F, 0, sizeof F);
+    int n = 0;
+    for (int f : r->filters) {
+        RingFrame& fr = s.ring[f];
+        if (!fr.has_depth) continue;
+        FilterView& V = F.nb[n++];
+        V.depth = static_cast<const float*>(fr.depth.ptr);
+        V.W = fr.w;
+        V.H = fr.h;
+        double R[9], t[3];
+        const pmsp_pose& rp = s.ring[r->ref].pose;
+        compose_rel(rp, fr.pose, R, t);
+        for (int k = 0; k < 9; ++k) V.Rf[k] = (float)R[k];
+        for (int k = 0; k < 3; ++k) V.tf[k] = (float)t[k];
+        compose_rel(fr.pose, rp, R, t);
+        for (int k = 0; k < 9; ++k) V.Rb[k] = (float)R[k];
+        for (int k = 0; k < 3; ++k) V.tb[k] = (float)t[k];
+    }
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        F.depth_in = base;
+        F.depth_out = filtered;
+        F.agree = nullptr;
+        F.W = r->W;
+        F.H = r->H;
+        F.n = n;
+        F.min_views = r->min_views;
+        F.max_px = r->max_px;
+        e = launch_filter_kernel(F, s.stream);
+    } else {
+        e = cudaMemcpyAsync(filtered, base, N * 4, cudaMemcpyDeviceToDevice, s.stream);
+    }
+    RingFrame& ref = s.ring[r->ref];
+    if (e == cudaSuccess && dev_alloc(ref.depth, N * 4) == PMSP_OK) {
+        e = cudaMemcpyAsync(ref.depth.ptr, base, N * 4, cudaMemcpyDeviceToDevice, s.stream);
+        ref.has_depth = true;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(r->done, s.stream);
+    return e == cudaSuccess ? PMSP_OK : PMSP_ECUDA;
+}
+
+void scheduler(Serving* sp) {
+    Serving& s = *sp;
+    cudaSetDevice(s.ctx->device);
+    int slot = 0;
+    std::vector<int4> work;
+    std::vector<PixelParams> probs;
+    for (;;) {
+        std::vector<Request*> step_reqs;
+        {
+            std::unique_lock<std::mutex> lk(s.mu);
+            // retire finished requests whose completion event has fired
+            for (size_t k = 0; k < s.finishing.size();) {
+                Request* r = s.finishing[k];
+                const cudaError_t q = cudaEventQuery(r->done);
+                if (q == cudaSuccess || q != cudaErrorNotReady) {
+                    r->status = q == cudaSuccess ? DONE : FAILED;
+                    if (q != cudaSuccess) r->fail_code = PMSP_ECUDA;
+                    s.stats.completed += q == cudaSuccess;
+                    s.finishing.erase(s.finishing.begin() + k);
+                    s.cv_done.notify_all();
+                } else {
+                    ++k;
+                }
+            }
+            // admission: FIFO, while a slot is free and the maps fit
+            while (!s.queue.empty() && (int)s.active.size() < s.ctx->max_active) {
+                Request* r = s.queue.front();
+                if (s.bytes_in_use + r->bytes > s.ctx->mem_cap) break;
+                if (cudaMallocAsync(&r->maps.ptr, r->bytes, s.stream) != cudaSuccess) {
+                    r->maps.ptr = nullptr;
+                    break;  // retried next step
+                }
+                r->maps.bytes = r->bytes;
+                if (cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) break;
+                s.queue.pop_front();
+                s.bytes_in_use += r->bytes;
+                fill_request(s, r);
+                r->status = ACTIVE;
+                r->phase = 0;
+                s.active.push_back(r);
+            }
+            s.stats.queued = (uint32_t)s.queue.size();
+            s.stats.active = (uint32_t)s.active.size();
+            s.stats.bytes_in_use = s.bytes_in_use;
+            if (s.stop) break;
+            if (s.active.empty()) {
+                s.cv_work.wait_for(lk, std::chrono::milliseconds(s.finishing.empty() ? 20 : 1));
+                continue;
+            }
+            step_reqs = s.active;
+            probs.resize(step_reqs.size());
+            work.clear();
+            for (size_t k = 0; k < step_reqs.size(); ++k) {
+                Request* r = step_reqs[k];
+                probs[k] = r->prob;
+                probs[k].phase = r->phase;
+                const int tw = (r->W + TILE_W - 1) / TILE_W, th = (r->H + TILE_H - 1) / TILE_H;
+                for (int ty = 0; ty < th; ++ty)
+                    for (int tx = 0; tx < tw; ++tx) work.push_back(make_int4((int)k, tx * TILE_W, ty * TILE_H, 0));
+            }
+        }
+        // the pinned staging slot must be free (its previous step has run)
+        if (s.slot_busy[slot] && !wait_event(s.slot_ev[slot], STEP_DEADLINE_S)) {
+            std::lock_guard<std::mutex> lk(s.mu);
+            s.err = "scheduler step did not complete within the deadline";
+            fail_all(s, s.active, PMSP_ETIMEDOUT);
+            s.cv_done.notify_all();
+            continue;
+        }
+        const size_t pb = probs.size() * sizeof(PixelParams), wb = work.size() * sizeof(int4);
+        int rc = ensure_host(s.h_problems[slot], s.h_problems_bytes[slot], pb);
+        if (!rc) rc = ensure_host(s.h_work[slot], s.h_work_bytes[slot], wb);
+        if (!rc) {
+            // device buffers are reused by every step on the one stream: grow only when idle
+            if (s.d_problems.bytes < pb || s.d_work.bytes < wb) cudaStreamSynchronize(s.stream);
+            rc = dev_alloc(s.d_problems, pb);
+            if (!rc) rc = dev_alloc(s.d_work, wb);
+            if (!rc) rc = dev_alloc(s.d_counter, sizeof(unsigned));
+        }
+        cudaError_t e = cudaSuccess;
+        if (!rc) {
+            memcpy(s.h_problems[slot], probs.data(), pb);
+            memcpy(s.h_work[slot], work.data(), wb);
+            e = cudaMemcpyAsync(s.d_problems.ptr, s.h_problems[slot], pb, cudaMemcpyHostToDevice, s.stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_work.ptr, s.h_work[slot], wb, cudaMemcpyHostToDevice, s.stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(s.d_counter.ptr, 0, sizeof(unsigned), s.stream);
+            if (e == cudaSuccess) {
+                BatchArgs a;
+                a.problems = static_cast<const PixelParams*>(s.d_problems.ptr);
+                a.work = static_cast<const int4*>(s.d_work.ptr);
+                a.n_work = (int)work.size();
+                a.phase = -2;
+                a.counter = static_cast<unsigned*>(s.d_counter.ptr);
+                int max_s = 1;
+                for (const PixelParams& p : probs) max_s = std::max(max_s, p.S);
+                const int bucket = batch_bucket(max_s);
+                const int grid = std::max(1, std::min(a.n_work, s.sms * batch_blocks_per_sm(bucket)));
+                e = batch_launch(bucket, a, grid, s.stream);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(s.slot_ev[slot], s.stream);
+        }
+        std::lock_guard<std::mutex> lk(s.mu);
+        if (rc || e != cudaSuccess) {
+            s.err = rc ? "scheduler allocation failed" : cudaGetErrorString(e);
+            fail_all(s, s.active, rc ? rc : PMSP_ECUDA);
+            s.cv_done.notify_all();
+            continue;
+        }
+        s.slot_busy[slot] = true;
+        slot ^= 1;
+        s.stats.steps++;
+        for (Request* r : step_reqs) {
+            if (++r->phase < r->n_phases) continue;
+            s.active.erase(std::find(s.active.begin(), s.active.end(), r));
+            if (enqueue_finish(s, r) != PMSP_OK) {
+                r->status = FAILED;
+                r->fail_code = PMSP_ECUDA;
+                s.cv_done.notify_all();
+                continue;
+            }
+            r->status = FINISHING;
+            s.finishing.push_back(r);
+        }
+    }
+}
+
+Serving& serving(pmsp_ctx* c) {
+    if (!c->serving) {
+        Serving* s = new Serving();
+        s->ctx = c;
+        s->ring.resize(c->ring_capacity);
+        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        for (auto& ev : s->slot_ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, c->device);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;  // keep freed request maps in the pool for the next admission
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        s->th = std::thread(scheduler, s);
+        c->serving = s;
+    }
+    return *c->serving;
+}
+
+int take(Serving& s, uint64_t ticket, pmsp_maps* out, pmsp_ctx* c) {
+    auto it = s.tickets.find(ticket);
+    if (it == s.tickets.end()) return ctx_fail(c, PMSP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Request* r = it->second;
+    if (r->status == FAILED) {
+        const int code = r->fail_code ? r->fail_code : PMSP_ECUDA;
+        s.tickets.erase(it);
+        release_request(s, r);
+        return ctx_fail(c, code, "request failed: %s", s.err.c_str());
+    }
+    if (r->status != DONE) return PMSP_EBUSY;
+    int rc = PMSP_OK;
+    if (out) {
+        const size_t N = (size_t)r->W * r->H;
+        if (out->w != r->W || out->h != r->H || !out->depth)
+            return ctx_fail(c, PMSP_EINVAL, "output maps must be %dx%d", r->W, r->H);
+        const float* base = static_cast<const float*>(r->maps.ptr);
+        const cudaMemcpyKind k = out->memory == PMSP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        cudaError_t e = cudaMemcpy(out->depth, base + 5 * N, N * 4, k);
+        if (e == cudaSuccess && out->normal) e = cudaMemcpy(out->normal, base + N, 3 * N * 4, k);
+        if (e == cudaSuccess && out->cost) e = cudaMemcpy(out->cost, base + 4 * N, N * 4, k);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "result copy");
+    }
+    s.tickets.erase(it);
+    release_request(s, r);
+    return rc;
+}
+
+}  // namespace
+
+void runtime_shutdown(pmsp_ctx* c) {
+    if (c->serving) {
+        Serving& s = *c->serving;
+        {
+            std::lock_guard<std::mutex> lk(s.mu);
+            s.stop = true;
+        }
+        s.cv_work.notify_all();
+        if (s.th.joinable()) s.th.join();
+        cudaStreamSynchronize(s.stream);
+        for (auto& kv : s.tickets) {
+            Request* r = kv.second;
+            if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, s.stream);
+            if (r->done) cudaEventDestroy(r->done);
+            delete r;
+        }
+        cudaStreamSynchronize(s.stream);
+        for (auto& f : s.ring) {
+            free_texture(f.tex);
+            if (f.lin.ptr) cudaFree(f.lin.ptr);
+            if (f.depth.ptr) cudaFree(f.depth.ptr);
+        }
+        for (DevBuffer* d : {&s.d_problems, &s.d_work, &s.d_counter})
+            if (d->ptr) cudaFree(d->ptr);
+        for (int k = 0; k < 2; ++k) {
+            if (s.h_problems[k]) cudaFreeHost(s.h_problems[k]);
+            if (s.h_work[k]) cudaFreeHost(s.h_work[k]);
+            if (s.slot_ev[k]) cudaEventDestroy(s.slot_ev[k]);
+        }
+        cudaStreamDestroy(s.stream);
+        delete c->serving;
+        c->serving = nullptr;
+    }
+    batch_shutdown(c);
+}
+
+}  // namespace pmsp
+
+using namespace pmsp;
+
+extern "C" {
+
+int pmsp_ring_push(pmsp_ctx* c, int64_t id, const pmsp_image* img, const pmsp_pose* pose) {
+    if (!c) return PMSP_EINVAL;
+    cudaSetDevice(c->device);
+    int rc = check_image(c, img, "ring frame");
+    if (rc) return rc;
+    if (!pose) return ctx_fail(c, PMSP_EINVAL, "NULL pose");
+    Serving& s = serving(c);
+    std::lock_guard<std::mutex> lk(s.mu);
+    int slot = find_frame(s, id);
+    if (slot >= 0 && s.ring[slot].pins > 0) return ctx_fail(c, PMSP_EBUSY, "frame %lld is in use", (long long)id);
+    if (slot < 0) {
+        for (int i = 0; i < (int)s.ring.size() && slot < 0; ++i)
+            if (!s.ring[i].used) slot = i;
+        if (slot < 0) {  // evict the oldest unused frame
+            uint64_t best = UINT64_MAX;
+            for (int i = 0; i < (int)s.ring.size(); ++i)
+                if (s.ring[i].pins == 0 && s.ring[i].seq < best) best = s.ring[i].seq, slot = i;
+        }
+        if (slot < 0) return ctx_fail(c, PMSP_EBUSY, "every ring frame is used by a request");
+    }
+    RingFrame& f = s.ring[slot];
+    // the slot's previous contents may still be read by finished work on the serving stream
+    cudaStreamSynchronize(s.stream);
+    const size_t row = (size_t)img->w * format_bytes(img->format);
+    if (dev_alloc(f.lin, row * img->h) != PMSP_OK) return ctx_fail(c, PMSP_ENOMEM, "ring frame allocation");
+    const cudaMemcpyKind k = img->memory == PMSP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpy2DAsync(f.lin.ptr, row, img->data, img->pitch_bytes, row, img->h, k, s.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ring upload");
+    const cudaStream_t saved = c->stream;
+    c->stream = s.stream;
+    rc = upload_texture(c, f.tex, img);
+    c->stream = saved;
+    if (rc) return rc;
+    e = cudaStreamSynchronize(s.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ring upload");
+    f.id = id;
+    f.used = true;
+    f.seq = ++s.push_seq;
+    f.w = img->w;
+    f.h = img->h;
+    f.fmt = img->format;
+    f.pose = *pose;
+    f.has_depth = false;
+    return PMSP_OK;
+}
+
+int pmsp_submit(pmsp_ctx* c, const pmsp_request* q, uint64_t* ticket) {
+    if (!c) return PMSP_EINVAL;
+    cudaSetDevice(c->device);
+    if (!q || !ticket) return ctx_fail(c, PMSP_EINVAL, "NULL request or ticket");
+    int rc = check_params(c, &q->params, q->n_src);
+    if (rc) return rc;
+    if (q->n_filter < 0 || q->n_filter > PMSP_MAX_SOURCES || (q->n_filter > 0 && !q->filter_frames) ||
+        !q->src_frames)
+        return ctx_fail(c, PMSP_EINVAL, "bad frame lists");
+    if (q->n_filter > 0 && (!(q->max_reproj_px > 0.f) || q->min_views < 0))
+        return ctx_fail(c, PMSP_EINVAL, "bad filter parameters");
+    Serving& s = serving(c);
+    std::lock_guard<std::mutex> lk(s.mu);
+    Request tmp;
+    tmp.ref = find_frame(s, q->ref_frame);
+    if (tmp.ref < 0) return ctx_fail(c, PMSP_ENOTFOUND, "reference frame %lld not in the ring", (long long)q->ref_frame);
+    for (int k = 0; k < q->n_src; ++k) {
+        const int f = find_frame(s, q->src_frames[k]);
+        if (f < 0) return ctx_fail(c, PMSP_ENOTFOUND, "source frame %lld not in the ring", (long long)q->src_frames[k]);
+        tmp.srcs.push_back(f);
+    }
+    for (int k = 0; k < q->n_filter; ++k) {
+        const int f = find_frame(s, q->filter_frames[k]);
+        if (f < 0) return ctx_fail(c, PMSP_ENOTFOUND, "filter frame %lld not in the ring", (long long)q->filter_frames[k]);
+        tmp.filters.push_back(f);
+    }
+    const RingFrame& ref = s.ring[tmp.ref];
+    if (ref.w & 1) return ctx_fail(c, PMSP_EINVAL, "reference width %d must be even", ref.w);
+    Request* r = new Request(std::move(tmp));
+    r->params = q->params;
+    r->max_px = q->max_reproj_px;
+    r->min_views = q->min_views;
+    r->W = ref.w;
+    r->H = ref.h;
+    r->n_phases = 2 + 2 * q->params.iterations;
+    r->bytes = (size_t)r->W * r->H * 6 * sizeof(float);
+    if (r->bytes > c->mem_cap) {
+        delete r;
+        s.stats.rejected++;
+        return ctx_fail(c, PMSP_EADMIT, "request needs %zu bytes, above the cap", (size_t)r->W * r->H * 24);
+    }
+    for (int f : r->srcs) s.ring[f].pins++;
+    for (int f : r->filters) s.ring[f].pins++;
+    s.ring[r->ref].pins++;
+    r->ticket = s.next_ticket++;
+    s.tickets[r->ticket] = r;
+    s.queue.push_back(r);
+    s.stats.submitted++;
+    *ticket = r->ticket;
+    s.cv_work.notify_all();
+    return PMSP_OK;
+}
+
+int pmsp_poll(pmsp_ctx* c, uint64_t ticket, pmsp_maps* out) {
+    if (!c) return PMSP_EINVAL;
+    cudaSetDevice(c->device);
+    Serving& s = serving(c);
+    std::lock_guard<std::mutex> lk(s.mu);
+    return take(s, ticket, out, c);
+}
+
+int pmsp_wait(pmsp_ctx* c, uint64_t ticket, int timeout_ms, pmsp_maps* out) {
+    if (!c) return PMSP_EINVAL;
+    cudaSetDevice(c->device);
+    Serving& s = serving(c);
+    std::unique_lock<std::mutex> lk(s.mu);
+    const auto until = Clock::now() + std::chrono::milliseconds(std::max(0, timeout_ms));
+    for (;;) {
+        const int rc = take(s, ticket, out, c);
+        if (rc != PMSP_EBUSY) return rc;
+        if (s.cv_done.wait_until(lk, until) == std::cv_status::timeout) {
+            const int rc2 = take(s, ticket, out, c);
+            if (rc2 != PMSP_EBUSY) return rc2;
+            return ctx_fail(c, PMSP_ETIMEDOUT, "ticket %llu not finished after %d ms", (unsigned long long)ticket,
+                            timeout_ms);
+        }
+    }
+}
+
+int pmsp_get_serving_stats(pmsp_ctx* c, pmsp_serving_stats* out) {
+    if (!c || !out) return PMSP_EINVAL;
+    Serving& s = serving(c);
+    std::lock_guard<std::mutex> lk(s.mu);
+    *out = s.stats;
+    return PMSP_OK;
+}
+
+}  // extern "C"

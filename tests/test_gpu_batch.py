@@ -1,0 +1,124 @@
+"""Batched densification (persistent launch per phase, CUDA graph, autotuner).
+
+Every keyframe of a batch runs the single-keyframe per-pixel computation, so
+its maps must equal what pmsp_densify gives for it alone (compared bit for
+bit, with a cost tolerance of 1e-6 as the only slack for the compiler's
+instruction scheduling), and the oracle pins the values themselves.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2211_16266_gb300 as pm
+    return pm
+
+
+@pytest.fixture(scope="module")
+def ctx(pm):
+    import torch
+    c = pm.Context(0, stream=torch.cuda.current_stream())
+    yield c
+    c.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _problems():
+    out = []
+    p0 = scenes.config0()
+    out.append(p0)
+    p1 = scenes.config1(W=384, H=192)
+    out.append(p1)
+    p2 = scenes.trajectory_problem(250, 131, 3, seed_scene=1010)
+    p2.params = dict(d_min=0.3, d_max=10.0, patch_w=9, patch_stride=3, iterations=3, best_k=2, sigma_color=0.15,
+                     sigma_space=4.0, n_refine=6, neighbor_table=1, seed=5, keyframe_id=77)
+    out.append(p2)
+    p3 = scenes.trajectory_problem(320, 160, 8, seed_scene=1012, fmt="f16")
+    p3.params = dict(p1.params, iterations=5, keyframe_id=9)
+    out.append(p3)
+    p4 = scenes.trajectory_problem(128, 64, 4, seed_scene=1013)
+    p4.params = dict(p1.params, best_k=2, iterations=2, keyframe_id=11)
+    out.append(p4)
+    return out
+
+
+def _args(p):
+    return (_dev(p.ref.image), (p.ref.R, p.ref.t), [_dev(f.image) for f in p.srcs], [(f.R, f.t) for f in p.srcs])
+
+
+def test_batch_equals_single_keyframe_runs(pm, ctx):
+    probs = _problems()
+    args = [_args(p) for p in probs]
+    batch = pm.Batch([(*a, p.params, None) for a, p in zip(args, probs)])
+    outs = pm.pmsp_densify_batch(ctx, batch)
+    for a, p, o in zip(args, probs, outs):
+        single = pm.pmsp_densify(ctx, *a, p.params)
+        bd, bn, bc = o.numpy()
+        sd, sn, sc = single.numpy()
+        assert np.max(np.abs(bc - sc)) <= 1e-6
+        assert np.mean(bd == sd) >= 0.999
+
+
+def test_batch_matches_oracle(pm, ctx):
+    probs = _problems()[:3]
+    args = [_args(p) for p in probs]
+    outs = pm.pmsp_densify_batch(ctx, pm.Batch([(*a, p.params, None) for a, p in zip(args, probs)]))
+    for p, o in zip(probs, outs):
+        od, on, oc = oracle.Problem.from_scene(p).densify()
+        gd, _, gc = (x.astype(np.float64) for x in o.numpy())
+        assert np.mean(np.abs(gd - od) / od <= 5e-3) >= 0.995
+        assert np.mean(np.abs(gc - oc) <= 1e-4) >= 0.995
+
+
+def test_graph_replay_and_host_batches(pm, ctx):
+    probs = _problems()
+    args = [_args(p) for p in probs]
+    batch = pm.Batch([(*a, p.params, None) for a, p in zip(args, probs)])
+    first = [tuple(x.copy() for x in o.numpy()) for o in pm.pmsp_densify_batch(ctx, batch, pm.PMSP_BATCH_GRAPH)]
+    for o in batch.outs:                       # poison the outputs, then replay the captured graph
+        o.depth.fill_(-1.0)
+    pm.pmsp_densify_batch(ctx, batch, pm.PMSP_BATCH_GRAPH)
+    pm.pmsp_sync(ctx)
+    for f, o in zip(first, batch.outs):
+        for x, y in zip(f, o.numpy()):
+            assert np.array_equal(x, y)
+    # the same problems from host memory
+    hb = pm.Batch([(p.ref.image, (p.ref.R, p.ref.t), [f.image for f in p.srcs], [(f.R, f.t) for f in p.srcs],
+                    p.params, None) for p in probs])
+    for f, o in zip(first, pm.pmsp_densify_batch(ctx, hb)):
+        for x, y in zip(f, o.numpy()):
+            assert np.array_equal(x, y)
+
+
+def test_autotune_returns_valid_setting(pm, ctx):
+    probs = _problems()[:2]
+    args = [_args(p) for p in probs]
+    batch = pm.Batch([(*a, dict(p.params, patch_stride=1, patch_w=7), None) for a, p in zip(args, probs)])
+    t = pm.pmsp_autotune(ctx, batch, 0.01)
+    assert t.strategy in (0, 1) and t.order in (0, 1) and t.patch_stride in (0, 2)
+    assert t.blocks_per_sm >= (1 if t.strategy == 0 else 0)
+    outs = pm.pmsp_densify_batch(ctx, batch, 0, t)
+    for o in outs:
+        d = o.depth.cpu().numpy()
+        assert np.all(np.isfinite(d)) and d.min() >= 0.3 - 1e-6 and d.max() <= 10.0 + 1e-5
+
+
+def test_batch_rejects_bad_item(pm, ctx):
+    probs = _problems()[:2]
+    args = [_args(p) for p in probs]
+    bad = dict(probs[1].params, best_k=9)
+    with pytest.raises(pm.PmspError) as e:
+        pm.pmsp_densify_batch(ctx, pm.Batch([(*args[0], probs[0].params, None), (*args[1], bad, None)]))
+    assert e.value.code == pm.PMSP_EINVAL

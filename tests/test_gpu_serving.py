@@ -1,0 +1,161 @@
+"""Serving runtime: frame ring, admission, continuous batching, bounded waits.
+
+Each request's maps must not depend on what else shares its launches: a
+request served alone, served in a mix of other sizes and view counts, and
+densified by pmsp_densify give the same maps.
+"""
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2211_16266_gb300 as pm
+    return pm
+
+
+def _frames(W, H, n, seed_scene=1001, fmt="u8"):
+    traj = scenes.trajectory(n, seed=2000)
+    scene = scenes.Scene(seed=seed_scene)
+    scene.objects = scenes.place_objects(seed_scene + 77, [c for _, _, c in traj], n=20)
+    out = []
+    for (R, t, C) in traj:
+        img, _ = scene.render(R, t, W, H, ss=1, with_range=False)
+        im = scenes.quantise_u8(img) if fmt == "u8" else (img / 255.0).astype(np.float16)
+        out.append((im, (R, t)))
+    return out
+
+
+PARAMS = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=4, best_k=3, sigma_color=0.2,
+              sigma_space=3.0, n_refine=6, neighbor_table=0, seed=42, keyframe_id=3)
+
+
+def _push(pm, ctx, frames, base):
+    for k, (im, pose) in enumerate(frames):
+        pm.pmsp_ring_push(ctx, base + k, im, pose)
+
+
+def _maps(pm, W, H):
+    return pm.Maps.empty(W, H)
+
+
+def test_alone_equals_in_mix_equals_single(pm):
+    import torch
+    fa = _frames(384, 192, 7)
+    fb = _frames(256, 128, 5, seed_scene=1020)
+    fc = _frames(512, 256, 9, seed_scene=1021, fmt="f16")
+    with pm.Context(0, ring_capacity=32) as ctx:
+        _push(pm, ctx, fa, 100)
+        _push(pm, ctx, fb, 200)
+        _push(pm, ctx, fc, 300)
+        srcs_a = [100, 101, 102, 104, 105, 106]
+        t = pm.pmsp_submit(ctx, 103, srcs_a, PARAMS)
+        alone = pm.pmsp_wait(ctx, t, 60000, _maps(pm, 384, 192))
+        # the same request among others of different sizes and view counts
+        others = [pm.pmsp_submit(ctx, 202, [200, 201, 203, 204], dict(PARAMS, best_k=2, keyframe_id=5)),
+                  pm.pmsp_submit(ctx, 304, [300, 301, 302, 303, 305, 306, 307, 308], dict(PARAMS, iterations=6)),
+                  pm.pmsp_submit(ctx, 201, [200, 202], dict(PARAMS, best_k=1, iterations=2))]
+        t2 = pm.pmsp_submit(ctx, 103, srcs_a, PARAMS)
+        more = [pm.pmsp_submit(ctx, 303, [300, 301, 302, 304, 305], dict(PARAMS, keyframe_id=8))]
+        mixed = pm.pmsp_wait(ctx, t2, 60000, _maps(pm, 384, 192))
+        for tk in others + more:
+            pm.pmsp_wait(ctx, tk, 60000, None)
+        for a, b in zip(alone.numpy(), mixed.numpy()):
+            assert np.array_equal(a, b)
+        st = pm.pmsp_get_serving_stats(ctx)
+        assert st["completed"] == 6 and st["active"] == 0 and st["queued"] == 0
+        # the plain per-keyframe path gives the same maps
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        single = pm.pmsp_densify(ctx, dev(fa[3][0]), fa[3][1], [dev(fa[k][0]) for k in (0, 1, 2, 4, 5, 6)],
+                                 [fa[k][1] for k in (0, 1, 2, 4, 5, 6)], PARAMS)
+        sd, sn, sc = single.numpy()
+        ad, an, ac = alone.numpy()
+        assert np.max(np.abs(sc - ac)) <= 1e-6 and np.mean(sd == ad) >= 0.999
+
+
+def test_admission_slots_memory_and_errors(pm):
+    fa = _frames(256, 128, 5)
+    # one slot: requests run one after another and all finish
+    with pm.Context(0, max_active=1, ring_capacity=8) as ctx:
+        _push(pm, ctx, fa, 0)
+        ts = [pm.pmsp_submit(ctx, 2, [0, 1, 3, 4], dict(PARAMS, keyframe_id=k)) for k in range(4)]
+        for t in ts:
+            pm.pmsp_wait(ctx, t, 60000, None)
+        assert pm.pmsp_get_serving_stats(ctx)["completed"] == 4
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_poll(ctx, ts[0])
+        assert e.value.code == pm.PMSP_ENOTFOUND          # released after retrieval
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_submit(ctx, 99, [0, 1], dict(PARAMS, best_k=2))
+        assert e.value.code == pm.PMSP_ENOTFOUND          # frame not in the ring
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_submit(ctx, 2, [0, 1], dict(PARAMS, best_k=3))
+        assert e.value.code == pm.PMSP_EINVAL
+    # a memory cap below one request's maps rejects it at submission
+    with pm.Context(0, mem_cap_bytes=256 * 128 * 8, ring_capacity=8) as ctx:
+        _push(pm, ctx, fa, 0)
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_submit(ctx, 2, [0, 1, 3, 4], PARAMS)
+        assert e.value.code == pm.PMSP_EADMIT
+    # a cap of two requests' maps admits two at a time; all still finish
+    with pm.Context(0, mem_cap_bytes=2 * 256 * 128 * 24, ring_capacity=8) as ctx:
+        _push(pm, ctx, fa, 0)
+        ts = [pm.pmsp_submit(ctx, 2, [0, 1, 3, 4], dict(PARAMS, keyframe_id=k)) for k in range(5)]
+        for t in ts:
+            pm.pmsp_wait(ctx, t, 60000, None)
+
+
+def test_bounded_wait_times_out_then_completes(pm):
+    fa = _frames(1024, 512, 7)
+    with pm.Context(0, ring_capacity=8) as ctx:
+        _push(pm, ctx, fa, 0)
+        t = pm.pmsp_submit(ctx, 3, [0, 1, 2, 4, 5, 6], dict(PARAMS, iterations=8))
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_wait(ctx, t, 0, None)
+        assert e.value.code == pm.PMSP_ETIMEDOUT
+        assert pm.pmsp_poll(ctx, t) is None or True      # still running or already done
+        pm.pmsp_wait(ctx, t, 120000, None)
+
+
+def test_ring_eviction_and_pinning(pm):
+    fa = _frames(128, 64, 6)
+    with pm.Context(0, ring_capacity=4) as ctx:
+        for k in range(4):
+            pm.pmsp_ring_push(ctx, k, *fa[k])
+        pm.pmsp_ring_push(ctx, 4, *fa[4])                 # evicts frame 0
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_submit(ctx, 2, [0, 1], dict(PARAMS, best_k=2))
+        assert e.value.code == pm.PMSP_ENOTFOUND
+        t = pm.pmsp_submit(ctx, 2, [1, 3, 4], dict(PARAMS, best_k=2))
+        # every frame is now in use: a push must not evict them
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_ring_push(ctx, 5, *fa[5])
+        assert e.value.code == pm.PMSP_EBUSY
+        pm.pmsp_wait(ctx, t, 60000, None)
+        pm.pmsp_ring_push(ctx, 5, *fa[5])                 # frames released with the ticket
+
+
+def test_filter_against_finished_neighbours(pm):
+    fa = _frames(384, 192, 9)
+    with pm.Context(0, ring_capacity=16) as ctx:
+        _push(pm, ctx, fa, 0)
+        nb = {}
+        for k in (2, 3, 5, 6):
+            srcs = [j for j in range(k - 2, k + 3) if j != k and 0 <= j < 9]
+            nb[k] = pm.pmsp_wait(ctx, pm.pmsp_submit(ctx, k, srcs, dict(PARAMS, keyframe_id=k)), 60000,
+                                 _maps(pm, 384, 192))
+        srcs = [1, 2, 3, 5, 6, 7]
+        t = pm.pmsp_submit(ctx, 4, srcs, dict(PARAMS, keyframe_id=4), filter_frames=[2, 3, 5, 6])
+        out = pm.pmsp_wait(ctx, t, 60000, _maps(pm, 384, 192))
+        raw = pm.pmsp_wait(ctx, pm.pmsp_submit(ctx, 4, srcs, dict(PARAMS, keyframe_id=4)), 60000,
+                           _maps(pm, 384, 192))
+        want, _ = pm.pmsp_consistency_filter(ctx, raw.depth, fa[4][1], [nb[k].depth for k in (2, 3, 5, 6)],
+                                             [fa[k][1] for k in (2, 3, 5, 6)], 1.0, 2)
+        assert np.array_equal(out.depth, want)
+        assert 0.2 < np.mean(out.depth > 0) < 1.0
