@@ -324,8 +324,222 @@ def run_reference(args):
                           e2e=dict(value=val, unit="keyframes/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))))
 
 
+BATCH_CLASSES = ((960, 480, 12), (1920, 960, 14), (3840, 1920, 6))
+
+
+class ClassFrames:
+    """Frames of one resolution class rendered along one trajectory (ss=1)."""
+
+    def __init__(self, W, H, n, seed, fmt):
+        import scenes
+        self.W, self.H = W, H
+        traj = scenes.trajectory(n, seed=seed)
+        scene = scenes.Scene(seed=1003)
+        scene.objects = scenes.place_objects(1080, [c for _, _, c in traj], n=20)
+        self.frames = []
+        for (R, t, C) in traj:
+            img, _ = scene.render(R, t, W, H, ss=1, with_range=False)
+            im = scenes.quantise_u8(img) if fmt == "u8" else (img / 255.0).astype(np.float16)
+            self.frames.append((im, (R, t)))
+
+
+def batched_problems(fmt, seed=3000):
+    """32 keyframes: 12 at 960x480, 14 at 1920x960, 6 at 3840x1920, 4-10 sources each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for ci, (W, H, count) in enumerate(BATCH_CLASSES):
+        cf = ClassFrames(W, H, 2 * count + 11, 2000 + ci, fmt)
+        for k in range(count):
+            centre = 5 + 2 * k
+            S = int(rng.integers(4, 11))
+            offs = [o for o in (-1, 1, -2, 2, -3, 3, -4, 4, -5, 5)][:S]
+            params = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=ITERS, best_k=3,
+                          sigma_color=0.2, sigma_space=3.0, n_refine=6, neighbor_table=0, seed=42,
+                          keyframe_id=1000 * ci + k)
+            out.append((cf.frames[centre], [cf.frames[centre + o] for o in offs], params))
+    return out
+
+
+def run_batched(args):
+    """Config: 32 mixed keyframes in one batch (persistent/concurrent launches, CUDA graph,
+    autotuned), FP16 storage, against the plain per-keyframe path on uint8 images."""
+    import torch
+    import paper_2211_16266_gb300 as pm
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pm.Context(0, stream=stream)
+    res = {}
+    for fmt in ("f16", "u8"):
+        probs = batched_problems(fmt)
+        to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        cache = {}
+        def d(im):
+            key = id(im)
+            if key not in cache:
+                cache[key] = to_dev(im)
+            return cache[key]
+        items = [(d(ref[0]), ref[1], [d(s[0]) for s in srcs], [s[1] for s in srcs], p) for ref, srcs, p in probs]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            outs = [pm.Maps.empty(it[0].shape[1], it[0].shape[0], device=dev) for it in items]
+            batch = pm.Batch([(*it, o) for it, o in zip(items, outs)])
+            tuning = pm.pmsp_autotune(ctx, batch, 0.0) if fmt == "f16" else None
+
+            def timed(fn, reps):
+                fn()
+                stream.synchronize()
+                ts = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    b.record(stream)
+                    stream.synchronize()
+                    ts.append(a.elapsed_time(b))
+                return float(np.median(ts))
+            if fmt == "f16":
+                res["batched_ms"] = timed(lambda: pm.pmsp_densify_batch(ctx, batch, pm.PMSP_BATCH_GRAPH, tuning),
+                                          max(2, args.steps))
+                res["tuning"] = dict(strategy=tuning.strategy, blocks_per_sm=tuning.blocks_per_sm,
+                                     order=tuning.order, patch_stride=tuning.patch_stride)
+            else:
+                def plain():
+                    for it, o in zip(items, outs):
+                        pm.pmsp_densify(ctx, *it, out=o)
+                res["plain_ms"] = timed(plain, max(2, args.steps))
+    n = sum(c for _, _, c in BATCH_CLASSES)
+    print(json.dumps(dict(
+        metric="keyframes/s, 32 mixed keyframes (12x960x480, 14x1920x960, 6x3840x1920), 4-10 views",
+        value=n / (res["batched_ms"] / 1e3), unit="keyframes/s", n_gpus=1, steps=args.steps, warmup=1,
+        ms_per_step=res["batched_ms"], higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f16 images, f32 math", data="synthetic",
+        config=dict(workload="batched form: one batch of 32 keyframes, CUDA graph, autotuned",
+                    tuning=res["tuning"], plain_per_keyframe_u8_ms=res["plain_ms"],
+                    plain_keyframes_per_s=n / (res["plain_ms"] / 1e3)))))
+    ctx.close()
+
+
+def run_serving(args):
+    """Config: Poisson requests (4/s, 1-s bursts at 12/s every 20 s) of mixed sizes served by
+    continuous batching over a 64-frame ring (FP16), against a FIFO of the plain
+    per-keyframe path (uint8) on the same arrival trace."""
+    import threading
+    import torch
+    import paper_2211_16266_gb300 as pm
+    n_req = args.requests
+    rng = np.random.default_rng(3000)
+    t, arrivals = 0.0, []
+    while len(arrivals) < n_req:
+        rate = 12.0 if (t % 20.0) < 1.0 else 4.0
+        t += rng.exponential(1.0 / rate)
+        arrivals.append(t)
+    weights = np.array([c for _, _, c in BATCH_CLASSES], float)
+    classes = rng.choice(3, size=n_req, p=weights / weights.sum())
+    views = rng.integers(4, 11, size=n_req)
+    out = {}
+    for mode, fmt in (("served", "f16"), ("plain", "u8")):
+        cfs = [ClassFrames(W, H, 24, 2000 + ci, fmt) for ci, (W, H, _) in enumerate(BATCH_CLASSES)]
+        lat = []
+        if mode == "served":
+            ctx = pm.Context(0, stream=None, ring_capacity=64)
+            counters = [0, 0, 0]
+            ids = [[], [], []]
+            next_id = [0]
+            maps = {ci: pm.Maps.empty(W, H) for ci, (W, H, _) in enumerate(BATCH_CLASSES)}
+            tickets = []
+
+            def push(ci):
+                cf = cfs[ci]
+                im, pose = cf.frames[counters[ci] % len(cf.frames)]
+                counters[ci] += 1
+                fid = next_id[0]
+                next_id[0] += 1
+                while True:
+                    try:
+                        pm.pmsp_ring_push(ctx, fid, im, pose)
+                        break
+                    except pm.PmspError as e:
+                        # back-pressure: every ring frame is held by queued or running
+                        # requests; take the oldest result to free its frames
+                        if e.code != pm.PMSP_EBUSY or not tickets:
+                            raise
+                        tk, c2, ts = tickets.pop(0)
+                        pm.pmsp_wait(ctx, tk, 600000, maps[c2])
+                        lat.append(time.perf_counter() - ts)
+                ids[ci].append(fid)
+                return fid
+            for ci in range(3):           # warm the ring: 10 frames per class
+                for _ in range(10):
+                    push(ci)
+            t0 = time.perf_counter()
+            for k in range(n_req):
+                now = time.perf_counter() - t0
+                if arrivals[k] > now:
+                    time.sleep(arrivals[k] - now)
+                ci = int(classes[k])
+                ref = push(ci)
+                S = int(views[k])
+                srcs = ids[ci][-(S + 1):-1]
+                p = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=ITERS, best_k=3,
+                         sigma_color=0.2, sigma_space=3.0, n_refine=6, neighbor_table=0, seed=42, keyframe_id=k)
+                tk = pm.pmsp_submit(ctx, ref, srcs, p)
+                tickets.append((tk, ci, t0 + arrivals[k]))  # latency counts from the arrival
+                # retrieve finished ones without blocking
+                for entry in list(tickets):
+                    if pm.pmsp_poll(ctx, entry[0], maps[entry[1]]) is not None:
+                        lat.append(time.perf_counter() - entry[2])
+                        tickets.remove(entry)
+            for (tk, ci, ts) in tickets:
+                pm.pmsp_wait(ctx, tk, 600000, maps[ci])
+                lat.append(time.perf_counter() - ts)
+            wall = time.perf_counter() - t0
+            ctx.close()
+        else:
+            dev = torch.device("cuda", 0)
+            ctx = pm.Context(0)
+            dframes = [[torch.from_numpy(np.ascontiguousarray(im)).to(dev) for im, _ in cf.frames] for cf in cfs]
+            torch.cuda.synchronize()
+            outs = {ci: pm.Maps.empty(W, H, device=dev) for ci, (W, H, _) in enumerate(BATCH_CLASSES)}
+            counters = [10, 10, 10]
+            t0 = time.perf_counter()
+            busy_until = 0.0
+            for k in range(n_req):
+                now = time.perf_counter() - t0
+                if arrivals[k] > now:
+                    time.sleep(arrivals[k] - now)
+                ci = int(classes[k])
+                n_f = len(cfs[ci].frames)
+                r = counters[ci]
+                counters[ci] += 1
+                S = int(views[k])
+                ref_i = r % n_f
+                src_i = [(r - j) % n_f for j in range(1, S + 1)]
+                p = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=ITERS, best_k=3,
+                         sigma_color=0.2, sigma_space=3.0, n_refine=6, neighbor_table=0, seed=42, keyframe_id=k)
+                # FIFO: the request waits for the previous ones (single worker), then runs alone
+                pm.pmsp_densify(ctx, dframes[ci][ref_i], cfs[ci].frames[ref_i][1], [dframes[ci][j] for j in src_i],
+                                [cfs[ci].frames[j][1] for j in src_i], p, out=outs[ci])
+                torch.cuda.synchronize()
+                lat.append(time.perf_counter() - t0 - arrivals[k])
+            wall = time.perf_counter() - t0
+            ctx.close()
+        lat = np.array(lat) * 1e3
+        out[mode] = dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                         keyframes_per_s=n_req / wall, wall_s=wall)
+    print(json.dumps(dict(
+        metric="p50/p99 latency and keyframes/s, Poisson 4/s + 12/s bursts, mixed sizes",
+        value=out["served"]["keyframes_per_s"], unit="keyframes/s", n_gpus=1, steps=n_req, warmup=0,
+        ms_per_step=1e3 * out["served"]["wall_s"] / n_req, higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f16 images, f32 math", data="synthetic",
+        latency_ms=dict(p50=out["served"]["p50_ms"], p99=out["served"]["p99_ms"]),
+        config=dict(workload=f"serving form: {n_req} requests over a 64-frame ring, continuous batching",
+                    plain_fifo_u8=out["plain"]))))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="keyframe", choices=["keyframe", "batched", "serving"])
+    ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -338,7 +552,12 @@ def main():
         return
     import __graft_entry__
     __graft_entry__.build()
-    run_gpu(args)
+    if args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
+    else:
+        run_gpu(args)
 
 
 if __name__ == "__main__":

@@ -233,15 +233,13 @@ void fill_problem(PixelParams& P, const pmsp_image* ref, const void* ref_dev, in
         compose_rel(*ref_pose, src_poses[s], R, t);
         SourceView& V = P.src[s];
         V.tex = tex[s];
-        for (int i = 0; i < 3; ++i) {
-            for (int j = 0; j < 3; ++j) V.m[4 * i + j] = (float)R[3 * i + j];
-            V.m[4 * i + 3] = (float)t[i];
-        }
+        for (int k = 0; k < 9; ++k) V.R[k] = (float)R[k];
+        for (int k = 0; k < 3; ++k) V.t[k] = (float)t[k];
         const double Ws = srcs[s].w, Hs = srcs[s].h;
-        V.m[12] = (float)(Ws / (2.0 * M_PI));
-        V.m[13] = (float)(0.5 * Ws - 0.5);
-        V.m[14] = (float)(-Hs / M_PI);
-        V.m[15] = (float)(0.5 * Hs - 0.5);
+        V.su = (float)(Ws / (2.0 * M_PI));
+        V.ou = (float)(0.5 * Ws - 0.5);
+        V.sv = (float)(-Hs / M_PI);
+        V.ov = (float)(0.5 * Hs - 0.5);
         V.inv_w = (float)(1.0 / Ws);
         V.inv_h = (float)(1.0 / Hs);
     }

@@ -41,7 +41,10 @@ struct RingFrame {
     DevBuffer lin;         // as a reference (row-major, unpadded)
     DevBuffer depth;       // depth of the last finished request with this reference
     bool has_depth = false;
+    bool loading = false;  // being rewritten by pmsp_ring_push
 };
+
+using TexKey = std::tuple<int, int, int>;  // w, h, format
 
 enum Status { QUEUED, ACTIVE, FINISHING, DONE, FAILED };
 
@@ -70,7 +73,10 @@ struct Serving {
     std::condition_variable cv_work, cv_done;
     std::thread th;
     bool stop = false;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // scheduler launches
+    cudaStream_t upload = nullptr;   // ring uploads
+    cudaEvent_t upload_ev = nullptr;
+    std::multimap<TexKey, TexImage> tex_pool;  // texture arrays kept for frames of their size
     std::vector<RingFrame> ring;
     uint64_t push_seq = 0;
     std::deque<Request*> queue;
@@ -122,12 +128,17 @@ int ensure_host(void*& p, size_t& have, size_t need) {
     return PMSP_OK;
 }
 
-int dev_alloc(DevBuffer& b, size_t bytes) {
+// Grow-only buffer, allocated and freed in stream order on `st` (no
+// device-wide synchronisation while other work runs).
+int dev_alloc(DevBuffer& b, size_t bytes, cudaStream_t st) {
     if (b.bytes >= bytes) return PMSP_OK;
-    if (b.ptr) cudaFree(b.ptr);
+    if (b.ptr) cudaFreeAsync(b.ptr, st);
     b.ptr = nullptr;
     b.bytes = 0;
-    if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) return PMSP_ENOMEM;
+    if (cudaMallocAsync(&b.ptr, bytes, st) != cudaSuccess) {
+        b.ptr = nullptr;
+        return PMSP_ENOMEM;
+    }
     b.bytes = bytes;
     return PMSP_OK;
 }
@@ -215,7 +226,7 @@ int enqueue_finish(Serving& s, Request* r) {
         e = cudaMemcpyAsync(filtered, base, N * 4, cudaMemcpyDeviceToDevice, s.stream);
     }
     RingFrame& ref = s.ring[r->ref];
-    if (e == cudaSuccess && dev_alloc(ref.depth, N * 4) == PMSP_OK) {
+    if (e == cudaSuccess && dev_alloc(ref.depth, N * 4, s.stream) == PMSP_OK) {
         e = cudaMemcpyAsync(ref.depth.ptr, base, N * 4, cudaMemcpyDeviceToDevice, s.stream);
         ref.has_depth = true;
     }
@@ -297,10 +308,9 @@ void scheduler(Serving* sp) {
         if (!rc) rc = ensure_host(s.h_work[slot], s.h_work_bytes[slot], wb);
         if (!rc) {
             // device buffers are reused by every step on the one stream: grow only when idle
-            if (s.d_problems.bytes < pb || s.d_work.bytes < wb) cudaStreamSynchronize(s.stream);
-            rc = dev_alloc(s.d_problems, pb);
-            if (!rc) rc = dev_alloc(s.d_work, wb);
-            if (!rc) rc = dev_alloc(s.d_counter, sizeof(unsigned));
+            rc = dev_alloc(s.d_problems, pb, s.stream);
+            if (!rc) rc = dev_alloc(s.d_work, wb, s.stream);
+            if (!rc) rc = dev_alloc(s.d_counter, sizeof(unsigned), s.stream);
         }
         cudaError_t e = cudaSuccess;
         if (!rc) {
@@ -355,6 +365,8 @@ Serving& serving(pmsp_ctx* c) {
         s->ctx = c;
         s->ring.resize(c->ring_capacity);
         cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&s->upload_ev, cudaEventDisableTiming);
         for (auto& ev : s->slot_ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, c->device);
         cudaMemPool_t pool;
@@ -415,6 +427,8 @@ void runtime_shutdown(pmsp_ctx* c) {
             delete r;
         }
         cudaStreamSynchronize(s.stream);
+        cudaStreamSynchronize(s.upload);
+        for (auto& kv : s.tex_pool) free_texture(kv.second);
         for (auto& f : s.ring) {
             free_texture(f.tex);
             if (f.lin.ptr) cudaFree(f.lin.ptr);
@@ -428,6 +442,8 @@ void runtime_shutdown(pmsp_ctx* c) {
             if (s.slot_ev[k]) cudaEventDestroy(s.slot_ev[k]);
         }
         cudaStreamDestroy(s.stream);
+        cudaStreamDestroy(s.upload);
+        cudaEventDestroy(s.upload_ev);
         delete c->serving;
         c->serving = nullptr;
     }
@@ -447,12 +463,12 @@ int pmsp_ring_push(pmsp_ctx* c, int64_t id, const pmsp_image* img, const pmsp_po
     if (rc) return rc;
     if (!pose) return ctx_fail(c, PMSP_EINVAL, "NULL pose");
     Serving& s = serving(c);
-    std::lock_guard<std::mutex> lk(s.mu);
+    std::unique_lock<std::mutex> lk(s.mu);
     int slot = find_frame(s, id);
     if (slot >= 0 && s.ring[slot].pins > 0) return ctx_fail(c, PMSP_EBUSY, "frame %lld is in use", (long long)id);
     if (slot < 0) {
         for (int i = 0; i < (int)s.ring.size() && slot < 0; ++i)
-            if (!s.ring[i].used) slot = i;
+            if (!s.ring[i].used && !s.ring[i].loading) slot = i;
         if (slot < 0) {  // evict the oldest unused frame
             uint64_t best = UINT64_MAX;
             for (int i = 0; i < (int)s.ring.size(); ++i)
@@ -460,21 +476,52 @@ int pmsp_ring_push(pmsp_ctx* c, int64_t id, const pmsp_image* img, const pmsp_po
         }
         if (slot < 0) return ctx_fail(c, PMSP_EBUSY, "every ring frame is used by a request");
     }
+    // Claim the slot: nothing uses an unpinned frame, so it is rewritten while
+    // the scheduler keeps running; the copies go on the upload stream so they
+    // do not queue behind the scheduler's launches.
     RingFrame& f = s.ring[slot];
-    // the slot's previous contents may still be read by finished work on the serving stream
-    cudaStreamSynchronize(s.stream);
+    f.used = false;
+    f.loading = true;
+    f.pins = 1;
+    const TexKey want(img->w, img->h, img->format);
+    if (f.tex.arr && TexKey(f.tex.w, f.tex.h, f.tex.fmt) != want) {  // keep arrays of other sizes for reuse
+        s.tex_pool.emplace(TexKey(f.tex.w, f.tex.h, f.tex.fmt), f.tex);
+        f.tex = TexImage{};
+    }
+    if (!f.tex.arr) {
+        auto it = s.tex_pool.find(want);
+        if (it != s.tex_pool.end()) {
+            f.tex = it->second;
+            s.tex_pool.erase(it);
+        }
+    }
+    lk.unlock();
     const size_t row = (size_t)img->w * format_bytes(img->format);
-    if (dev_alloc(f.lin, row * img->h) != PMSP_OK) return ctx_fail(c, PMSP_ENOMEM, "ring frame allocation");
+    cudaError_t e = cudaSuccess;
+    if (f.lin.bytes < row * img->h) {  // grow only, stream-ordered (no device-wide synchronisation)
+        if (f.lin.ptr) cudaFreeAsync(f.lin.ptr, s.upload);
+        f.lin.ptr = nullptr;
+        f.lin.bytes = 0;
+        e = cudaMallocAsync(&f.lin.ptr, row * img->h, s.upload);
+        if (e == cudaSuccess) f.lin.bytes = row * img->h;
+    }
     const cudaMemcpyKind k = img->memory == PMSP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    cudaError_t e = cudaMemcpy2DAsync(f.lin.ptr, row, img->data, img->pitch_bytes, row, img->h, k, s.stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ring upload");
-    const cudaStream_t saved = c->stream;
-    c->stream = s.stream;
-    rc = upload_texture(c, f.tex, img);
-    c->stream = saved;
-    if (rc) return rc;
-    e = cudaStreamSynchronize(s.stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ring upload");
+    if (e == cudaSuccess) e = cudaMemcpy2DAsync(f.lin.ptr, row, img->data, img->pitch_bytes, row, img->h, k, s.upload);
+    if (e == cudaSuccess) {
+        const cudaStream_t saved = c->stream;
+        c->stream = s.upload;
+        rc = upload_texture(c, f.tex, img);
+        c->stream = saved;
+    }
+    if (e == cudaSuccess && !rc) e = cudaEventRecord(s.upload_ev, s.upload);
+    const bool ok = e == cudaSuccess && !rc && wait_event(s.upload_ev, STEP_DEADLINE_S);
+    lk.lock();
+    f.loading = false;
+    f.pins = 0;
+    if (!ok) {
+        if (rc) return rc;
+        return e != cudaSuccess ? cuda_fail(c, e, "ring upload") : ctx_fail(c, PMSP_ETIMEDOUT, "ring upload timed out");
+    }
     f.id = id;
     f.used = true;
     f.seq = ++s.push_seq;
