@@ -254,6 +254,35 @@ int pmsp_densify_batch(pmsp_ctx* ctx, const pmsp_batch_item* items, int n, uint3
 int pmsp_autotune(pmsp_ctx* ctx, const pmsp_batch_item* items, int n, float max_changed,
                   pmsp_tuning* out);
 
+/*
+ * pmsp_densify_batch for callers that cannot allocate device memory when they
+ * densify. (The paper has no counterpart: this serves integration, not the
+ * method.) Such callers include host frameworks that own all device memory
+ * and forbid plug-ins to allocate, real-time threads that must not take the
+ * allocator's locks or trigger device-wide synchronisation, and code running
+ * while a stream is being recorded.
+ *
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine. Source images are read with plain loads from the caller's buffers
+ * (no texture arrays), and the batch's working state lives in one fixed
+ * __device__ array of PMSP_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library keeps until the process exits. The results are the same
+ * computation as pmsp_densify_batch; the uint8 conversion of the plain loads
+ * may differ from the texture unit's in the last bit, so maps agree within
+ * the parity tolerances rather than bit for bit.
+ *   items   n keyframes, 1 <= n <= PMSP_NOALLOC_MAX_ITEMS, every image and map in
+ *           device memory; iterations <= 31
+ * Work is enqueued on the context's stream (the call returns once enqueued).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and each call resets it: calls whose work
+ * overlaps on the GPU (different streams or contexts on one device) race, so
+ * serialise them. PMSP_EINVAL for a batch above the limits or with host memory.
+ */
+#define PMSP_NOALLOC_MAX_ITEMS 16
+#define PMSP_NOALLOC_SCRATCH_BYTES (64 * 1024)
+int pmsp_densify_batch_noalloc(pmsp_ctx* ctx, const pmsp_batch_item* items, int n);
+
 /* ------------------------------------------------------------------------
  * Serving (the densification thread of Sec. III: keyframes arrive from the
  * SLAM front end, each is densified against a small neighbourhood of

@@ -117,6 +117,8 @@ _SIGS["pmsp_densify_batch"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_in
                                 ctypes.POINTER(pmsp_tuning)], ctypes.c_int)
 _SIGS["pmsp_autotune"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int, ctypes.c_float,
                            ctypes.POINTER(pmsp_tuning)], ctypes.c_int)
+_SIGS["pmsp_densify_batch_noalloc"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int], ctypes.c_int)
+PMSP_NOALLOC_MAX_ITEMS = 16
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.argtypes = _args
@@ -429,6 +431,14 @@ def pmsp_densify_batch(ctx, batch, flags=0, tuning=None):
     """Densify every problem of a Batch; returns the list of output Maps."""
     t = ctypes.byref(tuning) if tuning is not None else None
     ctx.check(_lib.pmsp_densify_batch(ctx.h, batch.items, len(batch), int(flags), t))
+    return batch.outs
+
+
+def pmsp_densify_batch_noalloc(ctx, batch):
+    """pmsp_densify_batch without any device allocation (device-memory batches
+    of at most PMSP_NOALLOC_MAX_ITEMS keyframes), for callers that must not
+    allocate when they densify; see include/pmsp.h."""
+    ctx.check(_lib.pmsp_densify_batch_noalloc(ctx.h, batch.items, len(batch)))
     return batch.outs
 
 
