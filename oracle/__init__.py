@@ -88,6 +88,8 @@ def _load():
             lib.orc_halfsweep.argtypes = [P, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int]
             lib.orc_densify.argtypes = [P, _dp, _dp, _dp]
             lib.orc_plane_sweep.argtypes = [P, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+            lib.orc_warp_init.argtypes = [P, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.POINTER(Pose), _dp, _dp,
+                                          _dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
             lib.orc_consistency_filter.argtypes = [
                 ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(Pose), ctypes.c_int,
                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_dp),
@@ -220,6 +222,24 @@ class Problem:
         d, n, c = self._maps()
         self._lib.orc_densify(ctypes.byref(self.c), _ptr(d), _ptr(n), _ptr(c))
         return d, n, c
+
+    def warp_init(self, prev_depth, prev_normal, prev_pose, ref_pose):
+        """Initialisation from the previous keyframe's plane map (Sec. III-B).
+        Returns depth, normal, cost, winning source index (-1: random) and the
+        'clear' mask (decisions away from their thresholds)."""
+        pd = np.ascontiguousarray(prev_depth, dtype=np.float64)
+        pn = np.ascontiguousarray(prev_normal, dtype=np.float64)
+        rel = Pose()
+        self._lib.orc_rel_pose(ctypes.byref(make_pose(*prev_pose)), ctypes.byref(make_pose(*ref_pose)),
+                               ctypes.byref(rel))
+        d, n, c = self._maps()
+        src = np.zeros((self.H, self.W), np.int32)
+        clear = np.zeros((self.H, self.W), np.int32)
+        ip = ctypes.POINTER(ctypes.c_int)
+        self._lib.orc_warp_init(ctypes.byref(self.c), pd.shape[1], pd.shape[0], _ptr(pd), _ptr(pn),
+                                ctypes.byref(rel), _ptr(d), _ptr(n), _ptr(c), src.ctypes.data_as(ip),
+                                clear.ctypes.data_as(ip))
+        return d, n, c, src, clear.astype(bool)
 
     def plane_sweep(self, n_levels, normals):
         normals = np.ascontiguousarray(normals, dtype=np.float64).reshape(-1, 3)

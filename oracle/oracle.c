@@ -477,3 +477,99 @@ void orc_consistency_filter(int W, int H, const double* depth, const orc_pose* p
             if (margin) margin[i] = mg;
         }
 }
+
+/* ------------------------------------------------------ plane-map warping */
+
+/*
+ * Initialisation by plane-map warping (Sec. III-B: the optimised plane map of
+ * the preceding keyframe is transferred into the current one, after Shen
+ * 2013; the algorithm figure is missing, so this follows the project's
+ * reading). Every previous pixel j with range d_j > 0 is lifted to 3-D with
+ * its plane, moved into the current camera (rel: previous -> current) and
+ * splatted onto the nearest current pixel; per pixel the candidate with the
+ * smallest range wins (ties: smallest j). A winning plane is re-intersected
+ * with the pixel's own ray; if that is invalid (grazing, behind, or outside
+ * [d_min, d_max]) or no candidate reached the pixel, the random plane of the
+ * ordinary initialisation is used. Costs are those of the chosen planes.
+ * `src` (nullable) receives the winning j or -1; `clear` (nullable) is 1
+ * where every decision is at least 1e-3 px (rounding) and 1e-5 relative
+ * (range order) from its threshold.
+ */
+void orc_warp_init(const orc_problem* pb, int Wp, int Hp, const double* prev_depth, const double* prev_normal,
+                   const orc_pose* rel, double* depth, double* normal, double* cost, int* src, int* clear) {
+    const int W = pb->ref.W, H = pb->ref.H;
+    const size_t N = (size_t)W * H, Np = (size_t)Wp * Hp;
+    double* best = (double*)malloc(N * sizeof(double));
+    double* second = (double*)malloc(N * sizeof(double));
+    int* who = (int*)malloc(N * sizeof(int));
+    int* ok = (int*)malloc(N * sizeof(int));
+    for (size_t i = 0; i < N; ++i) { best[i] = INFINITY; second[i] = INFINITY; who[i] = -1; ok[i] = 1; }
+    for (int v = 0; v < Hp; ++v)
+        for (int u = 0; u < Wp; ++u) {
+            size_t j = (size_t)v * Wp + u;
+            double d = prev_depth[j];
+            if (!(d > 0)) continue;
+            double r[3], X[3], Y[3], uc, vc;
+            orc_bearing(Wp, Hp, u, v, r);
+            X[0] = d * r[0]; X[1] = d * r[1]; X[2] = d * r[2];
+            apply_pose(rel, X, Y);
+            orc_project(W, H, Y, &uc, &vc);
+            double fu = floor(uc + 0.5), fv = floor(vc + 0.5);
+            int qu = wrap_i((int)fu, W), qv = clamp_i((int)fv, 0, H - 1);
+            size_t q = (size_t)qv * W + qu;
+            double rng = sqrt(dot3(Y, Y));
+            /* a point within 1e-3 px of a rounding boundary may land on the pixel
+               across it in a lower precision: both pixels are marked unclear */
+            double eu = uc + 0.5 - fu, ev = vc + 0.5 - fv;
+            int au = eu < 1e-3 ? -1 : (eu > 1.0 - 1e-3 ? 1 : 0);
+            int av = ev < 1e-3 ? -1 : (ev > 1.0 - 1e-3 ? 1 : 0);
+            if (au || av) {
+                for (int a = 0; a <= (au != 0); ++a)
+                    for (int b = 0; b <= (av != 0); ++b) {
+                        int pu = wrap_i((int)fu + a * au, W), pv = clamp_i((int)fv + b * av, 0, H - 1);
+                        ok[(size_t)pv * W + pu] = 0;
+                    }
+            }
+            if (rng < best[q] || (rng == best[q] && (int)j < who[q])) {
+                second[q] = best[q];
+                best[q] = rng;
+                who[q] = (int)j;
+            } else if (rng < second[q]) {
+                second[q] = rng;
+            }
+        }
+    (void)Np;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            size_t i = (size_t)v * W + u;
+            double rp[3], d = 0.0, n[3] = {0, 0, 0};
+            orc_bearing(W, H, u, v, rp);
+            int used = 0, clr = ok[i];
+            if (who[i] >= 0) {
+                size_t j = (size_t)who[i];
+                int ju = (int)(j % Wp), jv = (int)(j / Wp);
+                double r[3], X[3], Y[3], nj[3] = {prev_normal[j], prev_normal[Np + j], prev_normal[2 * Np + j]};
+                orc_bearing(Wp, Hp, ju, jv, r);
+                X[0] = prev_depth[j] * r[0]; X[1] = prev_depth[j] * r[1]; X[2] = prev_depth[j] * r[2];
+                apply_pose(rel, X, Y);
+                for (int a = 0; a < 3; ++a)
+                    n[a] = rel->R[3 * a] * nj[0] + rel->R[3 * a + 1] * nj[1] + rel->R[3 * a + 2] * nj[2];
+                double den = dot3(n, rp);
+                if (second[i] < INFINITY && (second[i] - best[i]) < 1e-5 * best[i]) clr = 0;
+                if (fabs(den) < 1e-4) clr = 0;
+                if (den < -1e-6) {
+                    d = dot3(n, Y) / den;
+                    if (fabs(d - pb->p.d_min) < 1e-6 * d || fabs(d - pb->p.d_max) < 1e-6 * d) clr = 0;
+                    used = d >= pb->p.d_min && d <= pb->p.d_max;
+                }
+            }
+            if (!used) orc_random_plane(pb, u, v, &d, n);
+            depth[i] = d;
+            normal[i] = n[0]; normal[N + i] = n[1]; normal[2 * N + i] = n[2];
+            cost[i] = orc_cost(pb, u, v, d, n, NULL);
+            if (src) src[i] = used ? who[i] : -1;
+            if (clear) clear[i] = clr;
+        }
+    free(best); free(second); free(who); free(ok);
+}
