@@ -154,6 +154,33 @@ int pmsp_cost_map(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pos
                   const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
                   const pmsp_params* p, pmsp_maps* planes);
 
+/*
+ * Initialisation by plane-map warping (Sec. III-B: the optimised plane map of
+ * the preceding keyframe is transferred into the current one, after Shen
+ * 2013): every previous plane with range > 0 is moved into the current
+ * camera and splatted onto the nearest pixel (the nearest surface wins, equal
+ * ranges the smaller previous pixel index); a claimed pixel re-intersects the
+ * plane with its own ray; unclaimed pixels, and planes grazing, behind or
+ * outside [d_min, d_max] there, take the random initial plane of pmsp_init.
+ * Then the initial costs.
+ *   prev, prev_pose   previous keyframe's maps (depth and normal read; any size,
+ *                     host or device) and pose
+ *   out               device maps of the reference size
+ *   src               optional device array of w*h int32: winning previous pixel
+ *                     index (row-major) or -1 where the random plane was used
+ */
+int pmsp_warp_init(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pose,
+                   const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
+                   const pmsp_params* p, const pmsp_maps* prev, const pmsp_pose* prev_pose,
+                   pmsp_maps* out, int32_t* src);
+
+/* pmsp_densify with the warping initialisation in place of the random one
+ * (the paper's densification with "plane warping" on). */
+int pmsp_densify_warped(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pose,
+                        const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
+                        const pmsp_params* p, const pmsp_maps* prev, const pmsp_pose* prev_pose,
+                        pmsp_maps* out);
+
 /* Random initialisation (Sec. III-B) plus initial cost into out. */
 int pmsp_init(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pose,
               const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
@@ -288,10 +315,13 @@ int pmsp_densify_batch_noalloc(pmsp_ctx* ctx, const pmsp_batch_item* items, int 
  * SLAM front end, each is densified against a small neighbourhood of
  * keyframes, filtered against neighbouring depth maps and handed on).
  * Frames live in a device ring of the last ring_capacity pushes; requests
- * are admitted while a slot is free (max_active) and their maps fit under
- * mem_cap_bytes, and every scheduler step advances every admitted request by
- * one phase in one persistent launch (iteration-level continuous batching).
- * A request's maps do not depend on which other requests share its launches.
+ * are admitted in arrival order while a slot is free (max_active), their
+ * maps fit under mem_cap_bytes and the running requests' tiles stay within
+ * about two waves of the GPU's resident blocks (one request is always
+ * admitted). An admitted request's launch chain runs on a stream lane of its
+ * own, so requests that arrive while others run overlap with them on the
+ * device. A request's maps are exactly those pmsp_densify gives for it,
+ * whatever else is running.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int64_t ref_frame;            /* reference frame id (in the ring) */
@@ -307,7 +337,7 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, rejected;
     uint32_t queued, active;
-    uint64_t steps;               /* scheduler launches so far */
+    uint64_t steps;               /* requests started on a stream lane so far */
     uint64_t bytes_in_use;        /* maps of admitted and unretrieved requests */
 } pmsp_serving_stats;
 

@@ -119,6 +119,8 @@ _SIGS["pmsp_autotune"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int, ct
                            ctypes.POINTER(pmsp_tuning)], ctypes.c_int)
 _SIGS["pmsp_densify_batch_noalloc"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int], ctypes.c_int)
 PMSP_NOALLOC_MAX_ITEMS = 16
+_SIGS["pmsp_warp_init"] = ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M, _O, _M, _F], ctypes.c_int)
+_SIGS["pmsp_densify_warped"] = ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M, _O, _M], ctypes.c_int)
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.argtypes = _args
@@ -314,6 +316,32 @@ def pmsp_densify(ctx, ref, ref_pose, srcs, src_poses, params=None, out=None):
     m = out.c()
     ctx.check(_lib.pmsp_densify(ctx.h, ctypes.byref(cref), ctypes.byref(rp), cs, cp, n, ctypes.byref(p),
                                 ctypes.byref(m)))
+    return out
+
+
+def pmsp_warp_init(ctx, ref, ref_pose, srcs, src_poses, params, prev, prev_pose, out=None, src=None):
+    """Initialisation from the previous keyframe's maps (prev: Maps) by plane-map
+    warping; returns the output Maps (device) and, if `src` is given, fills it."""
+    keep = []
+    cref, rp, cs, cp, n, p = _problem(ref, ref_pose, srcs, src_poses, params, keep)
+    out = _out_maps(ref, out)
+    pm_ = prev.c()
+    m = out.c()
+    ctx.check(_lib.pmsp_warp_init(ctx.h, ctypes.byref(cref), ctypes.byref(rp), cs, cp, n, ctypes.byref(p),
+                                  ctypes.byref(pm_), ctypes.byref(make_pose(prev_pose)), ctypes.byref(m),
+                                  _ptr(src)))
+    return out
+
+
+def pmsp_densify_warped(ctx, ref, ref_pose, srcs, src_poses, params, prev, prev_pose, out=None):
+    """pmsp_densify starting from the previous keyframe's warped plane map."""
+    keep = []
+    cref, rp, cs, cp, n, p = _problem(ref, ref_pose, srcs, src_poses, params, keep)
+    out = _out_maps(ref, out)
+    pm_ = prev.c()
+    m = out.c()
+    ctx.check(_lib.pmsp_densify_warped(ctx.h, ctypes.byref(cref), ctypes.byref(rp), cs, cp, n, ctypes.byref(p),
+                                       ctypes.byref(pm_), ctypes.byref(make_pose(prev_pose)), ctypes.byref(m)))
     return out
 
 

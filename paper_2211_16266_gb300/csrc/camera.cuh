@@ -94,6 +94,48 @@ __device__ __forceinline__ float sample_bilinear(cudaTextureObject_t tex, float 
     return fmaf(fy, bot - top, top);
 }
 
+// ---- Two views at once: the same arithmetic on float2 pairs with the packed
+// FP32 instructions (fma/add/mul .f32x2), which issue once for both lanes.
+
+__device__ __forceinline__ float2 pair(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// atan(mn / mx) for two lanes (see atan_reduced).
+__device__ __forceinline__ float2 atan_reduced2(float2 mn, float2 mx) {
+    const float2 r = make_float2(__fdividef(mn.x, fmaxf(mx.x, 1e-30f)), __fdividef(mn.y, fmaxf(mx.y, 1e-30f)));
+    return mul2(r, atan_poly2(mul2(r, r)));
+}
+
+__device__ __forceinline__ float2 fast_atan2_pair(float2 y, float2 x) {
+    const float2 ax = make_float2(fabsf(x.x), fabsf(x.y)), ay = make_float2(fabsf(y.x), fabsf(y.y));
+    float2 a = atan_reduced2(make_float2(fminf(ax.x, ay.x), fminf(ax.y, ay.y)),
+                             make_float2(fmaxf(ax.x, ay.x), fmaxf(ax.y, ay.y)));
+    const float2 b = add2(pair(1.57079632679489662f), make_float2(-a.x, -a.y));
+    a.x = ay.x > ax.x ? b.x : a.x;
+    a.y = ay.y > ax.y ? b.y : a.y;
+    const float2 c = add2(pair(3.14159265358979324f), make_float2(-a.x, -a.y));
+    a.x = x.x < 0.f ? c.x : a.x;
+    a.y = x.y < 0.f ? c.y : a.y;
+    return make_float2(copysignf(a.x, y.x), copysignf(a.y, y.y));
+}
+
+__device__ __forceinline__ float2 fast_atan2_xpos_pair(float2 y, float2 x) {
+    const float2 ay = make_float2(fabsf(y.x), fabsf(y.y));
+    float2 a = atan_reduced2(make_float2(fminf(x.x, ay.x), fminf(x.y, ay.y)),
+                             make_float2(fmaxf(x.x, ay.x), fmaxf(x.y, ay.y)));
+    const float2 b = add2(pair(1.57079632679489662f), make_float2(-a.x, -a.y));
+    a.x = ay.x > x.x ? b.x : a.x;
+    a.y = ay.y > x.y ? b.y : a.y;
+    return make_float2(copysignf(a.x, y.x), copysignf(a.y, y.y));
+}
+
+__device__ __forceinline__ float2 floor_small2(float2 x) {
+    const float M = 12582912.0f;
+    return add2(__fadd2_rd(x, pair(M)), pair(-M));
+}
+
 __device__ __forceinline__ int wrap_index(int x, int W) {
     x %= W;
     return x < 0 ? x + W : x;

@@ -65,6 +65,15 @@ struct alignas(16) PixelParams {
     int colour;
     int iter;
     unsigned* err;
+    // Constants of views (2p, 2p + 1) interleaved, so one packed FP32
+    // instruction reads the same constant of both views (an odd last view is
+    // paired with itself).
+    struct ViewPair {
+        float2 R[9];
+        float2 t[3];
+        float2 su, ou, sv, ov;
+        float2 inv_w, inv_h;
+    } pairs[PMSP_MAX_SOURCES / 2];
 };
 
 struct FilterView {
@@ -81,6 +90,18 @@ struct FilterParams {
     int32_t* agree;
     int W, H, n, min_views;
     float max_px;
+};
+
+// Plane-map warping from the previous keyframe into the current one.
+struct WarpArgs {
+    const float* prev_depth;   // Wp x Hp, 0 = no plane
+    const float* prev_normal;  // 3 planes of Wp x Hp, previous camera frame
+    int Wp, Hp;
+    float R[9], t[3];          // previous camera -> current camera
+    int W, H;                  // current panorama
+    float su, ou, sv, ov;      // current projection scales
+    unsigned long long* zbuf;  // W x H claims (range bits << 32 | previous pixel)
+    int* src;                  // optional: winning previous pixel or -1
 };
 
 // Arguments of one launch of the persistent batched kernel.
@@ -100,6 +121,7 @@ template <int MAXS>
 cudaError_t launch_batch_kernel_t(const BatchArgs& a, int grid, cudaStream_t stream);
 cudaError_t launch_pixel_kernel(const PixelParams& p, int mode, cudaStream_t stream);
 cudaError_t launch_filter_kernel(const FilterParams& p, cudaStream_t stream);
+cudaError_t launch_warp_init(const PixelParams& p, const WarpArgs& a, cudaStream_t stream);
 cudaError_t launch_project_kernel(int W, int H, int n, const float* dirs, float* uc, float* vc,
                                   cudaStream_t stream);
 cudaError_t launch_sample_kernel(cudaTextureObject_t tex, int W, int H, int n, const float* uc,

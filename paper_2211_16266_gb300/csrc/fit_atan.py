@@ -117,6 +117,14 @@ def main():
             f.write(f"    float p = {float(np.float32(c[-1]))!r}f;\n")
             for ck in reversed(c[:-1]):
                 f.write(f"    p = fmaf(p, s, {float(np.float32(ck))!r}f);\n")
+            f.write("    return p;\n}\n\n")
+            f.write("// The same polynomial on two lanes with packed FP32 FMAs.\n")
+            f.write("__device__ __forceinline__ float2 atan_poly2(float2 s) {\n")
+            v = float(np.float32(c[-1]))
+            f.write(f"    float2 p = make_float2({v!r}f, {v!r}f);\n")
+            for ck in reversed(c[:-1]):
+                v = float(np.float32(ck))
+                f.write(f"    p = __ffma2_rn(p, s, make_float2({v!r}f, {v!r}f));\n")
             f.write("    return p;\n}\n\n}  // namespace pmsp\n")
         print("wrote", path)
 

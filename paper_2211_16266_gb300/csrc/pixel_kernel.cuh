@@ -23,6 +23,8 @@
 
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "camera.cuh"
 #include "common.cuh"
 #include "philox.cuh"
@@ -303,12 +305,163 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem
     return sum / (float)P.best_k;
 }
 
+// Intensities of views 2q and 2q + 1 at the projection of X: the projection
+// runs on float2 pairs (one packed instruction for both views), the two
+// gathers and the bilinear weights per view. The arithmetic is that of
+// view_sample, operation for operation.
+__device__ __forceinline__ float2 pair_sample(const PixelParams::ViewPair& VP, const SourceView& V0,
+                                              const SourceView& V1, float X, float Y, float Z) {
+    const float2 Xv = pair(X), Yv = pair(Y), Zv = pair(Z);
+    const float2 Yx = fma2(VP.R[0], Xv, fma2(VP.R[1], Yv, fma2(VP.R[2], Zv, VP.t[0])));
+    const float2 Yy = fma2(VP.R[3], Xv, fma2(VP.R[4], Yv, fma2(VP.R[5], Zv, VP.t[1])));
+    const float2 Yz = fma2(VP.R[6], Xv, fma2(VP.R[7], Yv, fma2(VP.R[8], Zv, VP.t[2])));
+    const float2 lon = fast_atan2_pair(Yx, Yz);
+    const float2 q = fma2(Yx, Yx, mul2(Yz, Yz));
+    const float2 rho = mul2(q, make_float2(rsqrtf(fmaxf(q.x, 1e-30f)), rsqrtf(fmaxf(q.y, 1e-30f))));
+    const float2 lat = fast_atan2_xpos_pair(make_float2(-Yy.x, -Yy.y), rho);
+    const float2 uc = fma2(lon, VP.su, VP.ou), vc = fma2(lat, VP.sv, VP.ov);
+    const float2 fi = floor_small2(uc), fj = floor_small2(vc);
+    const float2 fx = add2(uc, make_float2(-fi.x, -fi.y)), fy = add2(vc, make_float2(-fj.x, -fj.y));
+    const float2 xn = fma2(fi, VP.inv_w, VP.inv_w), yn = fma2(fj, VP.inv_h, VP.inv_h);
+    const float4 g0 = tex2Dgather<float4>(V0.tex, xn.x, yn.x, 0);
+    const float4 g1 = tex2Dgather<float4>(V1.tex, xn.y, yn.y, 0);
+    const float top0 = fmaf(fx.x, g0.z - g0.w, g0.w), bot0 = fmaf(fx.x, g0.y - g0.x, g0.x);
+    const float top1 = fmaf(fx.y, g1.z - g1.w, g1.w), bot1 = fmaf(fx.y, g1.y - g1.x, g1.x);
+    return make_float2(fmaf(fy.x, bot0 - top0, top0), fmaf(fy.y, bot1 - top1, top1));
+}
+
+// plane_cost for exactly NS >= 2 views held in kernel parameters, with the
+// views processed in pairs (packed FP32) and an odd last view on its own.
+template <int NS>
+__device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const TileSmem& sm, int lx, int ly,
+                                                   const RefStats& st, float3 rp, float d, float3 n) {
+    constexpr int NP = NS / 2;
+    constexpr bool ODD = (NS & 1) != 0;
+    const float eps = 1e-8f * st.Sw * st.Sw;
+    if (st.varI < eps) return 2.0f;
+    const float dn = d * (n.x * rp.x + n.y * rp.y + n.z * rp.z);
+    const int K = P.K, R = P.radius, stp = P.stride;
+    const int ac = K >> 1;
+
+    float2 c0[NP], SJ[NP], SJJ[NP], SIJ[NP];
+    float c0o = 0.f, SJo = 0.f, SJJo = 0.f, SIJo = 0.f;
+    {
+        const int o = ac * stp - R;
+        const float cl = sm.row_cos[ly + o];
+        const float3 rq = make_float3(cl * sm.col_sin[lx + o], -sm.row_sin[ly + o], cl * sm.col_cos[lx + o]);
+        const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+        if (!(den < -1e-6f)) return 2.0f;
+        const float t = __fdividef(dn, den);
+        const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            c0[q] = pair_sample(P.pairs[q], P.src[2 * q], P.src[2 * q + 1], X, Y, Z);
+            SJ[q] = SJJ[q] = SIJ[q] = pair(0.f);
+        }
+        if (ODD) c0o = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z);
+    }
+    bool valid = true;
+    for (int a = 0; a < K && valid; ++a) {
+        const int oy = a * stp - R;
+        const float cl = sm.row_cos[ly + oy], msl = -sm.row_sin[ly + oy];
+        const float* ref_row = sm.ref + (ly + oy) * TILE_PITCH + lx - R;
+        for (int b = 0; b < K; ++b) {
+            if (a == ac && b == ac) continue;
+            const float Iq = ref_row[b * stp];
+            const float w = bilateral(P, sm, a, b, Iq, st.Ip);
+            const float wI = w * (Iq - st.mu);
+            const int cx = lx + b * stp - R;
+            const float3 rq = make_float3(cl * sm.col_sin[cx], msl, cl * sm.col_cos[cx]);
+            const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+            if (!(den < -1e-6f)) {
+                valid = false;
+                break;
+            }
+            const float t = __fdividef(dn, den);
+            const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
+            const float2 w2 = pair(w), wI2 = pair(wI);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float2 J = pair_sample(P.pairs[q], P.src[2 * q], P.src[2 * q + 1], X, Y, Z);
+                const float2 Jc = add2(J, make_float2(-c0[q].x, -c0[q].y));
+                const float2 tw = mul2(w2, Jc);
+                SJ[q] = add2(SJ[q], tw);
+                SJJ[q] = fma2(tw, Jc, SJJ[q]);
+                SIJ[q] = fma2(wI2, Jc, SIJ[q]);
+            }
+            if (ODD) {
+                const float Jc = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z) - c0o;
+                const float tw = w * Jc;
+                SJo += tw;
+                SJJo = fmaf(tw, Jc, SJJo);
+                SIJo = fmaf(wI, Jc, SIJo);
+            }
+        }
+    }
+    if (!valid) return 2.0f;
+
+    float cs[NS];
+    auto view_cost = [&](float sj, float sjj, float sij) {
+        const float varJ = st.Sw * sjj - sj * sj;
+        const float cov = st.Sw * sij - st.SIc * sj;
+        if (varJ < eps) return 2.0f;
+        float ncc = cov * rsqrtf(st.varI * varJ);
+        ncc = fminf(1.0f, fmaxf(-1.0f, ncc));
+        return 1.0f - ncc;
+    };
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        cs[2 * q] = view_cost(SJ[q].x, SJJ[q].x, SIJ[q].x);
+        cs[2 * q + 1] = view_cost(SJ[q].y, SJJ[q].y, SIJ[q].y);
+    }
+    if (ODD) cs[NS - 1] = view_cost(SJo, SJJo, SIJo);
+#pragma unroll
+    for (int pass = 0; pass < NS; ++pass) {
+#pragma unroll
+        for (int s = (pass & 1); s + 1 < NS; s += 2) {
+            const float lo = fminf(cs[s], cs[s + 1]), hi = fmaxf(cs[s], cs[s + 1]);
+            cs[s] = lo;
+            cs[s + 1] = hi;
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        if (s < P.best_k) sum += cs[s];
+    return sum / (float)P.best_k;
+}
+
+// The cost used by the per-pixel kernels: the paired form where the views
+// are exactly known and sit in kernel parameters, the general one otherwise.
+template <int NS, bool EXACT, class VA>
+__device__ __forceinline__ float cost_of(const PixelParams& P, const TileSmem& sm, int lx, int ly,
+                                         const RefStats& st, float3 rp, float d, float3 n) {
+    if constexpr (EXACT && NS >= 2 && std::is_same<VA, ParamViews>::value)
+        return plane_cost_paired<NS>(P, sm, lx, ly, st, rp, d, n);
+    else
+        return plane_cost<NS, EXACT, VA>(P, sm, lx, ly, st, rp, d, n);
+}
+
 // Face the camera: n . r_p < 0 (|n . r_p| < 1e-3: replace by -r_p).
 __device__ __forceinline__ float3 face_camera(float3 n, float3 rp) {
     const float c = n.x * rp.x + n.y * rp.y + n.z * rp.z;
     if (fabsf(c) < 1e-3f) return make_float3(-rp.x, -rp.y, -rp.z);
     if (c > 0.f) return make_float3(-n.x, -n.y, -n.z);
     return n;
+}
+
+// Random initial plane of pixel i (Sec. III-B): inverse range uniform on
+// [1/d_max, 1/d_min), normal uniform on the sphere turned to the camera,
+// from Philox block (i, 0, 0, 0).
+__device__ __forceinline__ void random_plane(const PixelParams& P, size_t i, float3 rp, float& d, float3& n) {
+    const U4 u = draw_uniform4(i, 0, 0, P.seed, P.keyframe);
+    const float inv = fmaf(u.x, P.inv_dmin - P.inv_dmax, P.inv_dmax);
+    d = 1.0f / inv;
+    const float z = 1.0f - 2.0f * u.y;
+    const float rho = sqrtf(fmaxf(0.f, 1.0f - z * z));
+    float sp, cp;
+    sincospif(2.0f * u.z, &sp, &cp);
+    n = face_camera(make_float3(rho * cp, rho * sp, z), rp);
 }
 
 // One tile of one problem: stage the reference tile, then every active
@@ -333,23 +486,18 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm,
 
     if (MODE == MODE_COST) {
         const float3 n = make_float3(P.nx[i], P.ny[i], P.nz[i]);
-        P.cost[i] = plane_cost<NS, EXACT, VA>(P, sm, lx, ly, st, rp, P.depth[i], n);
+        P.cost[i] = cost_of<NS, EXACT, VA>(P, sm, lx, ly, st, rp, P.depth[i], n);
         return;
     }
     if (MODE == MODE_INIT) {
-        const U4 u = draw_uniform4(i, 0, 0, P.seed, P.keyframe);
-        const float inv = fmaf(u.x, P.inv_dmin - P.inv_dmax, P.inv_dmax);
-        const float d = 1.0f / inv;
-        const float z = 1.0f - 2.0f * u.y;
-        const float rho = sqrtf(fmaxf(0.f, 1.0f - z * z));
-        float sp, cp;
-        sincospif(2.0f * u.z, &sp, &cp);
-        const float3 n = face_camera(make_float3(rho * cp, rho * sp, z), rp);
+        float d;
+        float3 n;
+        random_plane(P, i, rp, d, n);
         P.depth[i] = d;
         P.nx[i] = n.x;
         P.ny[i] = n.y;
         P.nz[i] = n.z;
-        P.cost[i] = plane_cost<NS, EXACT, VA>(P, sm, lx, ly, st, rp, d, n);
+        P.cost[i] = cost_of<NS, EXACT, VA>(P, sm, lx, ly, st, rp, d, n);
         return;
     }
 
@@ -390,7 +538,7 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm,
             nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
         }
         if (ok) {
-            const float c = plane_cost<NS, EXACT, VA>(P, sm, lx, ly, st, rp, dc, nc);
+            const float c = cost_of<NS, EXACT, VA>(P, sm, lx, ly, st, rp, dc, nc);
             if (c < bc) {
                 bc = c;
                 bd = dc;

@@ -243,6 +243,19 @@ void fill_problem(PixelParams& P, const pmsp_image* ref, const void* ref_dev, in
         V.inv_w = (float)(1.0 / Ws);
         V.inv_h = (float)(1.0 / Hs);
     }
+    for (int q = 0; 2 * q < n_src; ++q) {
+        const SourceView& A = P.src[2 * q];
+        const SourceView& B = P.src[2 * q + 1 < n_src ? 2 * q + 1 : 2 * q];
+        PixelParams::ViewPair& VP = P.pairs[q];
+        for (int k = 0; k < 9; ++k) VP.R[k] = make_float2(A.R[k], B.R[k]);
+        for (int k = 0; k < 3; ++k) VP.t[k] = make_float2(A.t[k], B.t[k]);
+        VP.su = make_float2(A.su, B.su);
+        VP.ou = make_float2(A.ou, B.ou);
+        VP.sv = make_float2(A.sv, B.sv);
+        VP.ov = make_float2(A.ov, B.ov);
+        VP.inv_w = make_float2(A.inv_w, B.inv_w);
+        VP.inv_h = make_float2(A.inv_h, B.inv_h);
+    }
     P.ref = static_cast<const uint8_t*>(ref_dev);
     P.ref_pitch = ref_pitch;
     P.ref_format = ref->format;
@@ -380,7 +393,8 @@ int pmsp_destroy(pmsp_ctx* c) {
     runtime_shutdown(c);
     for (auto& t : c->src_tex) free_texture(t);
     free_texture(c->sample_tex);
-    for (DevBuffer* b : {&c->ref_stage, &c->map_stage, &c->filter_stage, &c->sample_stage})
+    for (DevBuffer* b : {&c->ref_stage, &c->map_stage, &c->filter_stage, &c->sample_stage, &c->warp_zbuf,
+                         &c->warp_prev})
         if (b->ptr) cudaFree(b->ptr);
     if (c->d_err) cudaFree(c->d_err);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -415,6 +429,95 @@ int pmsp_densify(pmsp_ctx* c, const pmsp_image* ref, const pmsp_pose* ref_pose, 
         P.colour = colour;
         if ((rc = launch(c, P, MODE_INIT))) return rc;
     }
+    for (int it = 0; it < p->iterations; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+            P.colour = colour;
+            P.iter = it;
+            if ((rc = launch(c, P, MODE_SWEEP))) return rc;
+        }
+    return finish_maps(c, out, P, true);
+}
+
+}  // extern "C"
+
+namespace pmsp {
+
+// Warping initialisation into P's planes, then the initial costs.
+static int warp_init_into(pmsp_ctx* c, PixelParams& P, const pmsp_maps* prev, const pmsp_pose* prev_pose,
+                          const pmsp_pose* ref_pose, int32_t* src) {
+    if (!prev || !prev->depth || !prev->normal || !prev_pose)
+        return ctx_fail(c, PMSP_EINVAL, "previous keyframe: depth, normal and pose are required");
+    if (prev->w < 2 || prev->h < 1 || (prev->memory != PMSP_HOST && prev->memory != PMSP_DEVICE))
+        return ctx_fail(c, PMSP_EINVAL, "previous keyframe: bad maps");
+    WarpArgs A;
+    memset(&A, 0, sizeof A);
+    A.Wp = prev->w;
+    A.Hp = prev->h;
+    const size_t Np = (size_t)A.Wp * A.Hp;
+    int rc;
+    if (prev->memory == PMSP_DEVICE) {
+        A.prev_depth = prev->depth;
+        A.prev_normal = prev->normal;
+    } else {
+        if ((rc = ensure_buffer(c, c->warp_prev, 4 * Np * sizeof(float)))) return rc;
+        float* base = static_cast<float*>(c->warp_prev.ptr);
+        cudaError_t e = cudaMemcpyAsync(base, prev->depth, Np * 4, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(base + Np, prev->normal, 3 * Np * 4, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "previous maps upload");
+        A.prev_depth = base;
+        A.prev_normal = base + Np;
+    }
+    double R[9], t[3];
+    compose_rel(*prev_pose, *ref_pose, R, t);  // previous camera -> current camera
+    for (int k = 0; k < 9; ++k) A.R[k] = (float)R[k];
+    for (int k = 0; k < 3; ++k) A.t[k] = (float)t[k];
+    A.W = P.W;
+    A.H = P.H;
+    A.su = (float)(P.W / (2.0 * M_PI));
+    A.ou = (float)(0.5 * P.W - 0.5);
+    A.sv = (float)(-P.H / M_PI);
+    A.ov = (float)(0.5 * P.H - 0.5);
+    if ((rc = ensure_buffer(c, c->warp_zbuf, (size_t)P.W * P.H * sizeof(unsigned long long)))) return rc;
+    A.zbuf = static_cast<unsigned long long*>(c->warp_zbuf.ptr);
+    A.src = src;
+    cudaError_t e = launch_warp_init(P, A, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "warp launch");
+    for (int colour = 0; colour < 2; ++colour) {
+        P.colour = colour;
+        if ((rc = launch(c, P, MODE_COST))) return rc;
+    }
+    return PMSP_OK;
+}
+
+}  // namespace pmsp
+
+extern "C" {
+
+int pmsp_warp_init(pmsp_ctx* c, const pmsp_image* ref, const pmsp_pose* ref_pose, const pmsp_image* srcs,
+                   const pmsp_pose* src_poses, int n_src, const pmsp_params* p, const pmsp_maps* prev,
+                   const pmsp_pose* prev_pose, pmsp_maps* out, int32_t* src) {
+    if (!c) return PMSP_EINVAL;
+    cudaSetDevice(c->device);
+    PixelParams P;
+    int rc = prepare_problem(c, ref, ref_pose, srcs, src_poses, n_src, p, P);
+    if (rc) return rc;
+    if ((rc = check_maps(c, out, ref->w, ref->h, true, true, "output"))) return rc;
+    if (out->memory != PMSP_DEVICE) return ctx_fail(c, PMSP_EINVAL, "pmsp_warp_init writes device maps only");
+    if ((rc = bind_maps(c, out, P, false))) return rc;
+    return warp_init_into(c, P, prev, prev_pose, ref_pose, src);
+}
+
+int pmsp_densify_warped(pmsp_ctx* c, const pmsp_image* ref, const pmsp_pose* ref_pose, const pmsp_image* srcs,
+                        const pmsp_pose* src_poses, int n_src, const pmsp_params* p, const pmsp_maps* prev,
+                        const pmsp_pose* prev_pose, pmsp_maps* out) {
+    if (!c) return PMSP_EINVAL;
+    cudaSetDevice(c->device);
+    PixelParams P;
+    int rc = prepare_problem(c, ref, ref_pose, srcs, src_poses, n_src, p, P);
+    if (rc) return rc;
+    if ((rc = check_maps(c, out, ref->w, ref->h, true, true, "output"))) return rc;
+    if ((rc = bind_maps(c, out, P, false))) return rc;
+    if ((rc = warp_init_into(c, P, prev, prev_pose, ref_pose, nullptr))) return rc;
     for (int it = 0; it < p->iterations; ++it)
         for (int colour = 0; colour < 2; ++colour) {
             P.colour = colour;

@@ -1,13 +1,15 @@
-// Serving runtime: device frame ring, admission by slots and memory, and a
-// scheduler thread that advances every admitted request by one phase per
-// launch of the persistent batched kernel (iteration-level continuous
-// batching). Paper Sec. III runs densification in its own thread fed by a
-// keyframe queue; this is that thread, reshaped for many concurrent
-// keyframes on one GPU.
+// Serving runtime: device frame ring, admission by slots, memory and resident
+// work, and a scheduler thread that starts every admitted request's launch
+// chain on a stream lane of its own, so requests that arrive while others run
+// are admitted as soon as a lane and memory free up and their kernels overlap
+// on the device (continuous batching at the granularity of the half-sweep
+// launches). Paper Sec. III runs densification in its own thread fed by a
+// keyframe queue; this is that thread, reshaped for many concurrent keyframes
+// on one GPU.
 //
-// Host waits are bounded: the scheduler polls CUDA events with a deadline
-// and fails the in-flight requests with PMSP_ETIMEDOUT instead of blocking;
-// pmsp_wait blocks on a condition variable up to the caller's timeout.
+// Host waits are bounded: the scheduler polls CUDA events and fails a request
+// with PMSP_ETIMEDOUT when it has not finished within a deadline; pmsp_wait
+// blocks on a condition variable up to the caller's timeout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,8 +60,10 @@ struct Request {
     float max_px = 1.f;
     int min_views = 2;
     int W = 0, H = 0;
-    int phase = 0, n_phases = 0;
-    size_t bytes = 0;
+    int n_phases = 0;
+    size_t bytes = 0, tiles = 0;
+    int lane = -1;
+    Clock::time_point admitted;
     DevBuffer maps;        // depth, nx, ny, nz, cost, filtered depth
     cudaEvent_t done = nullptr;
     PixelParams prob;
@@ -73,32 +77,29 @@ struct Serving {
     std::condition_variable cv_work, cv_done;
     std::thread th;
     bool stop = false;
-    cudaStream_t stream = nullptr;   // scheduler launches
+    std::vector<cudaStream_t> lanes;  // one running request per lane
+    std::vector<Request*> lane_req;
+    size_t running_tiles = 0;
     cudaStream_t upload = nullptr;   // ring uploads
     cudaEvent_t upload_ev = nullptr;
     std::multimap<TexKey, TexImage> tex_pool;  // texture arrays kept for frames of their size
     std::vector<RingFrame> ring;
     uint64_t push_seq = 0;
     std::deque<Request*> queue;
-    std::vector<Request*> active, finishing;
+    std::vector<Request*> running;
+    std::vector<Request*> zombies;  // overran the deadline and were given up on
     std::map<uint64_t, Request*> tickets;
     uint64_t next_ticket = 1;
     uint64_t bytes_in_use = 0;
     pmsp_serving_stats stats{};
-    // scheduler buffers (one pinned staging slot per in-flight step)
-    DevBuffer d_problems, d_work, d_counter;
-    void* h_problems[2] = {nullptr, nullptr};
-    void* h_work[2] = {nullptr, nullptr};
-    size_t h_problems_bytes[2] = {0, 0}, h_work_bytes[2] = {0, 0};
-    cudaEvent_t slot_ev[2] = {nullptr, nullptr};
-    bool slot_busy[2] = {false, false};
     int sms = 0;
     std::string err;
 };
 
 namespace {
 
-constexpr double STEP_DEADLINE_S = 60.0;
+constexpr double STEP_DEADLINE_S = 60.0;     // bound on a ring upload
+constexpr double REQUEST_DEADLINE_S = 600.0; // bound on one request's GPU work
 
 int find_frame(Serving& s, int64_t id) {
     for (int i = 0; i < (int)s.ring.size(); ++i)
@@ -118,16 +119,6 @@ bool wait_event(cudaEvent_t ev, double seconds) {
     }
 }
 
-int ensure_host(void*& p, size_t& have, size_t need) {
-    if (have >= need) return PMSP_OK;
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    have = 0;
-    if (cudaMallocHost(&p, need) != cudaSuccess) return PMSP_ENOMEM;
-    have = need;
-    return PMSP_OK;
-}
-
 // Grow-only buffer, allocated and freed in stream order on `st` (no
 // device-wide synchronisation while other work runs).
 int dev_alloc(DevBuffer& b, size_t bytes, cudaStream_t st) {
@@ -143,14 +134,19 @@ int dev_alloc(DevBuffer& b, size_t bytes, cudaStream_t st) {
     return PMSP_OK;
 }
 
+// Tiles of resident work admission aims for: about two waves of the sweep
+// kernel's resident blocks. More would only stretch every running request's
+// latency; a request that alone exceeds it still runs.
+size_t tile_budget(const Serving& s) { return (size_t)s.sms * 6 * 2; }
+
 // Give back a request's frames and maps (stream-ordered free: no device-wide sync).
 void release_request(Serving& s, Request* r) {
     for (int f : r->srcs) s.ring[f].pins--;
     for (int f : r->filters) s.ring[f].pins--;
     s.ring[r->ref].pins--;
-    if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, s.stream);
+    if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, s.upload);
     if (r->done) cudaEventDestroy(r->done);
-    if (r->status == ACTIVE || r->status == FINISHING || r->status == DONE) s.bytes_in_use -= r->bytes;
+    if (r->maps.ptr) s.bytes_in_use -= r->bytes;
     delete r;
 }
 
@@ -178,17 +174,17 @@ void fill_request(Serving& s, Request* r) {
     r->prob.err = s.ctx->d_err;
 }
 
-void fail_all(Serving& s, std::vector<Request*>& v, int code) {
-    for (Request* r : v) {
-        r->status = FAILED;
-        r->fail_code = code;
+// A request's whole launch chain on its lane: initialisation, the red/black
+// half-sweeps, the consistency filter against the named neighbours whose
+// depth maps exist, the copy of its depth into the ring, the completion event.
+int enqueue_request(Serving& s, Request* r, cudaStream_t st) {
+    PixelParams P = r->prob;
+    cudaError_t e = cudaSuccess;
+    for (int ph = 0; ph < r->n_phases && e == cudaSuccess; ++ph) {
+        P.colour = ph & 1;
+        P.iter = ph < 2 ? 0 : (ph - 2) >> 1;
+        e = launch_pixel_kernel(P, ph < 2 ? MODE_INIT : MODE_SWEEP, st);
     }
-    v.clear();
-}
-
-// The finishing step of a request: consistency filter against the depth maps
-// of the named neighbours that exist, then remember this depth in the ring.
-int enqueue_finish(Serving& s, Request* r) {
     const size_t N = (size_t)r->W * r->H;
     float* base = static_cast<float*>(r->maps.ptr);
     float* filtered = base + 5 * N;
@@ -211,8 +207,7 @@ int enqueue_finish(Serving& s, Request* r) {
         for (int k = 0; k < 9; ++k) V.Rb[k] = (float)R[k];
         for (int k = 0; k < 3; ++k) V.tb[k] = (float)t[k];
     }
-    cudaError_t e = cudaSuccess;
-    if (n > 0) {
+    if (e == cudaSuccess && n > 0) {
         F.depth_in = base;
         F.depth_out = filtered;
         F.agree = nullptr;
@@ -221,141 +216,95 @@ int enqueue_finish(Serving& s, Request* r) {
         F.n = n;
         F.min_views = r->min_views;
         F.max_px = r->max_px;
-        e = launch_filter_kernel(F, s.stream);
-    } else {
-        e = cudaMemcpyAsync(filtered, base, N * 4, cudaMemcpyDeviceToDevice, s.stream);
+        e = launch_filter_kernel(F, st);
+    } else if (e == cudaSuccess) {
+        e = cudaMemcpyAsync(filtered, base, N * 4, cudaMemcpyDeviceToDevice, st);
     }
     RingFrame& ref = s.ring[r->ref];
-    if (e == cudaSuccess && dev_alloc(ref.depth, N * 4, s.stream) == PMSP_OK) {
-        e = cudaMemcpyAsync(ref.depth.ptr, base, N * 4, cudaMemcpyDeviceToDevice, s.stream);
-        ref.has_depth = true;
+    if (e == cudaSuccess) {  // the ring's depth buffer was sized when the frame was pushed
+        e = cudaMemcpyAsync(ref.depth.ptr, base, N * 4, cudaMemcpyDeviceToDevice, st);
+        ref.has_depth = e == cudaSuccess;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(r->done, s.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(r->done, st);
     return e == cudaSuccess ? PMSP_OK : PMSP_ECUDA;
 }
 
 void scheduler(Serving* sp) {
     Serving& s = *sp;
     cudaSetDevice(s.ctx->device);
-    int slot = 0;
-    std::vector<int4> work;
-    std::vector<PixelParams> probs;
+    std::unique_lock<std::mutex> lk(s.mu);
     for (;;) {
-        std::vector<Request*> step_reqs;
-        {
-            std::unique_lock<std::mutex> lk(s.mu);
-            // retire finished requests whose completion event has fired
-            for (size_t k = 0; k < s.finishing.size();) {
-                Request* r = s.finishing[k];
-                const cudaError_t q = cudaEventQuery(r->done);
-                if (q == cudaSuccess || q != cudaErrorNotReady) {
-                    r->status = q == cudaSuccess ? DONE : FAILED;
-                    if (q != cudaSuccess) r->fail_code = PMSP_ECUDA;
-                    s.stats.completed += q == cudaSuccess;
-                    s.finishing.erase(s.finishing.begin() + k);
-                    s.cv_done.notify_all();
-                } else {
-                    ++k;
-                }
-            }
-            // admission: FIFO, while a slot is free and the maps fit
-            while (!s.queue.empty() && (int)s.active.size() < s.ctx->max_active) {
-                Request* r = s.queue.front();
-                if (s.bytes_in_use + r->bytes > s.ctx->mem_cap) break;
-                if (cudaMallocAsync(&r->maps.ptr, r->bytes, s.stream) != cudaSuccess) {
-                    r->maps.ptr = nullptr;
-                    break;  // retried next step
-                }
-                r->maps.bytes = r->bytes;
-                if (cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) break;
-                s.queue.pop_front();
-                s.bytes_in_use += r->bytes;
-                fill_request(s, r);
-                r->status = ACTIVE;
-                r->phase = 0;
-                s.active.push_back(r);
-            }
-            s.stats.queued = (uint32_t)s.queue.size();
-            s.stats.active = (uint32_t)s.active.size();
-            s.stats.bytes_in_use = s.bytes_in_use;
-            if (s.stop) break;
-            if (s.active.empty()) {
-                s.cv_work.wait_for(lk, std::chrono::milliseconds(s.finishing.empty() ? 20 : 1));
+        // retire requests whose completion event has fired (or that overran the deadline)
+        for (size_t k = 0; k < s.running.size();) {
+            Request* r = s.running[k];
+            const cudaError_t q = cudaEventQuery(r->done);
+            const bool late = q == cudaErrorNotReady &&
+                              Clock::now() - r->admitted > std::chrono::duration<double>(REQUEST_DEADLINE_S);
+            if (q == cudaErrorNotReady && !late) {
+                ++k;
                 continue;
             }
-            step_reqs = s.active;
-            probs.resize(step_reqs.size());
-            work.clear();
-            for (size_t k = 0; k < step_reqs.size(); ++k) {
-                Request* r = step_reqs[k];
-                probs[k] = r->prob;
-                probs[k].phase = r->phase;
-                const int tw = (r->W + TILE_W - 1) / TILE_W, th = (r->H + TILE_H - 1) / TILE_H;
-                for (int ty = 0; ty < th; ++ty)
-                    for (int tx = 0; tx < tw; ++tx) work.push_back(make_int4((int)k, tx * TILE_W, ty * TILE_H, 0));
+            r->status = q == cudaSuccess ? DONE : FAILED;
+            if (q != cudaSuccess) {
+                r->fail_code = late ? PMSP_ETIMEDOUT : PMSP_ECUDA;
+                s.err = late ? "request did not finish within the deadline" : cudaGetErrorString(q);
             }
-        }
-        // the pinned staging slot must be free (its previous step has run)
-        if (s.slot_busy[slot] && !wait_event(s.slot_ev[slot], STEP_DEADLINE_S)) {
-            std::lock_guard<std::mutex> lk(s.mu);
-            s.err = "scheduler step did not complete within the deadline";
-            fail_all(s, s.active, PMSP_ETIMEDOUT);
+            s.stats.completed += q == cudaSuccess;
+            s.running_tiles -= r->tiles;
+            if (!late) s.lane_req[r->lane] = nullptr;  // a late request keeps its lane blocked
+            s.running.erase(s.running.begin() + k);
             s.cv_done.notify_all();
-            continue;
         }
-        const size_t pb = probs.size() * sizeof(PixelParams), wb = work.size() * sizeof(int4);
-        int rc = ensure_host(s.h_problems[slot], s.h_problems_bytes[slot], pb);
-        if (!rc) rc = ensure_host(s.h_work[slot], s.h_work_bytes[slot], wb);
-        if (!rc) {
-            // device buffers are reused by every step on the one stream: grow only when idle
-            rc = dev_alloc(s.d_problems, pb, s.stream);
-            if (!rc) rc = dev_alloc(s.d_work, wb, s.stream);
-            if (!rc) rc = dev_alloc(s.d_counter, sizeof(unsigned), s.stream);
-        }
-        cudaError_t e = cudaSuccess;
-        if (!rc) {
-            memcpy(s.h_problems[slot], probs.data(), pb);
-            memcpy(s.h_work[slot], work.data(), wb);
-            e = cudaMemcpyAsync(s.d_problems.ptr, s.h_problems[slot], pb, cudaMemcpyHostToDevice, s.stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_work.ptr, s.h_work[slot], wb, cudaMemcpyHostToDevice, s.stream);
-            if (e == cudaSuccess) e = cudaMemsetAsync(s.d_counter.ptr, 0, sizeof(unsigned), s.stream);
-            if (e == cudaSuccess) {
-                BatchArgs a;
-                a.problems = static_cast<const PixelParams*>(s.d_problems.ptr);
-                a.work = static_cast<const int4*>(s.d_work.ptr);
-                a.n_work = (int)work.size();
-                a.phase = -2;
-                a.counter = static_cast<unsigned*>(s.d_counter.ptr);
-                int max_s = 1;
-                for (const PixelParams& p : probs) max_s = std::max(max_s, p.S);
-                const int bucket = batch_bucket(max_s);
-                const int grid = std::max(1, std::min(a.n_work, s.sms * batch_blocks_per_sm(bucket)));
-                e = batch_launch(bucket, a, grid, s.stream);
+        // admission: FIFO while a lane is free, the maps fit and the resident work allows
+        while (!s.queue.empty()) {
+            Request* r = s.queue.front();
+            if ((int)s.running.size() >= s.ctx->max_active) break;
+            if (s.bytes_in_use + r->bytes > s.ctx->mem_cap) break;
+            if (s.running_tiles > 0 && s.running_tiles + r->tiles > tile_budget(s)) break;
+            int lane = -1;
+            for (int i = 0; i < (int)s.lanes.size() && lane < 0; ++i)
+                if (!s.lane_req[i]) lane = i;
+            if (lane < 0 && (int)s.lanes.size() < s.ctx->max_active) {
+                cudaStream_t st;
+                if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
+                s.lanes.push_back(st);
+                s.lane_req.push_back(nullptr);
+                lane = (int)s.lanes.size() - 1;
             }
-            if (e == cudaSuccess) e = cudaEventRecord(s.slot_ev[slot], s.stream);
-        }
-        std::lock_guard<std::mutex> lk(s.mu);
-        if (rc || e != cudaSuccess) {
-            s.err = rc ? "scheduler allocation failed" : cudaGetErrorString(e);
-            fail_all(s, s.active, rc ? rc : PMSP_ECUDA);
-            s.cv_done.notify_all();
-            continue;
-        }
-        s.slot_busy[slot] = true;
-        slot ^= 1;
-        s.stats.steps++;
-        for (Request* r : step_reqs) {
-            if (++r->phase < r->n_phases) continue;
-            s.active.erase(std::find(s.active.begin(), s.active.end(), r));
-            if (enqueue_finish(s, r) != PMSP_OK) {
+            if (lane < 0) break;
+            const cudaStream_t st = s.lanes[lane];
+            if (cudaMallocAsync(&r->maps.ptr, r->bytes, st) != cudaSuccess) {
+                r->maps.ptr = nullptr;
+                break;  // retried on the next pass
+            }
+            r->maps.bytes = r->bytes;
+            if (!r->done && cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) break;
+            s.queue.pop_front();
+            s.bytes_in_use += r->bytes;
+            fill_request(s, r);
+            r->lane = lane;
+            r->admitted = Clock::now();
+            if (enqueue_request(s, r, st) != PMSP_OK) {
                 r->status = FAILED;
                 r->fail_code = PMSP_ECUDA;
+                s.err = "launch failed";
                 s.cv_done.notify_all();
                 continue;
             }
-            r->status = FINISHING;
-            s.finishing.push_back(r);
+            r->status = ACTIVE;
+            s.lane_req[lane] = r;
+            s.running.push_back(r);
+            s.running_tiles += r->tiles;
+            s.stats.steps++;
         }
+        s.stats.queued = (uint32_t)s.queue.size();
+        s.stats.active = (uint32_t)s.running.size();
+        s.stats.bytes_in_use = s.bytes_in_use;
+        if (s.stop) break;
+        if (s.running.empty())
+            s.cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        else
+            s.cv_work.wait_for(lk, std::chrono::microseconds(200));
     }
 }
 
@@ -364,10 +313,8 @@ Serving& serving(pmsp_ctx* c) {
         Serving* s = new Serving();
         s->ctx = c;
         s->ring.resize(c->ring_capacity);
-        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
         cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking);
         cudaEventCreateWithFlags(&s->upload_ev, cudaEventDisableTiming);
-        for (auto& ev : s->slot_ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, c->device);
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
@@ -387,7 +334,10 @@ int take(Serving& s, uint64_t ticket, pmsp_maps* out, pmsp_ctx* c) {
     if (r->status == FAILED) {
         const int code = r->fail_code ? r->fail_code : PMSP_ECUDA;
         s.tickets.erase(it);
-        release_request(s, r);
+        if (code == PMSP_ETIMEDOUT)
+            s.zombies.push_back(r);  // its kernels may still run: keep its maps and frames until shutdown
+        else
+            release_request(s, r);
         return ctx_fail(c, code, "request failed: %s", s.err.c_str());
     }
     if (r->status != DONE) return PMSP_EBUSY;
@@ -419,29 +369,21 @@ void runtime_shutdown(pmsp_ctx* c) {
         }
         s.cv_work.notify_all();
         if (s.th.joinable()) s.th.join();
-        cudaStreamSynchronize(s.stream);
-        for (auto& kv : s.tickets) {
-            Request* r = kv.second;
-            if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, s.stream);
+        for (cudaStream_t st : s.lanes) cudaStreamSynchronize(st);
+        cudaStreamSynchronize(s.upload);
+        for (auto& kv : s.tickets) s.zombies.push_back(kv.second);
+        for (Request* r : s.zombies) {
+            if (r->maps.ptr) cudaFree(r->maps.ptr);
             if (r->done) cudaEventDestroy(r->done);
             delete r;
         }
-        cudaStreamSynchronize(s.stream);
-        cudaStreamSynchronize(s.upload);
         for (auto& kv : s.tex_pool) free_texture(kv.second);
         for (auto& f : s.ring) {
             free_texture(f.tex);
             if (f.lin.ptr) cudaFree(f.lin.ptr);
             if (f.depth.ptr) cudaFree(f.depth.ptr);
         }
-        for (DevBuffer* d : {&s.d_problems, &s.d_work, &s.d_counter})
-            if (d->ptr) cudaFree(d->ptr);
-        for (int k = 0; k < 2; ++k) {
-            if (s.h_problems[k]) cudaFreeHost(s.h_problems[k]);
-            if (s.h_work[k]) cudaFreeHost(s.h_work[k]);
-            if (s.slot_ev[k]) cudaEventDestroy(s.slot_ev[k]);
-        }
-        cudaStreamDestroy(s.stream);
+        for (cudaStream_t st : s.lanes) cudaStreamDestroy(st);
         cudaStreamDestroy(s.upload);
         cudaEventDestroy(s.upload_ev);
         delete c->serving;
@@ -505,6 +447,10 @@ int pmsp_ring_push(pmsp_ctx* c, int64_t id, const pmsp_image* img, const pmsp_po
         e = cudaMallocAsync(&f.lin.ptr, row * img->h, s.upload);
         if (e == cudaSuccess) f.lin.bytes = row * img->h;
     }
+    // the depth map a finished request leaves for later filters: sized here, while
+    // nothing reads the slot, so finishing requests only copy into it
+    if (e == cudaSuccess && dev_alloc(f.depth, (size_t)img->w * img->h * sizeof(float), s.upload) != PMSP_OK)
+        e = cudaErrorMemoryAllocation;
     const cudaMemcpyKind k = img->memory == PMSP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (e == cudaSuccess) e = cudaMemcpy2DAsync(f.lin.ptr, row, img->data, img->pitch_bytes, row, img->h, k, s.upload);
     if (e == cudaSuccess) {
@@ -569,6 +515,7 @@ int pmsp_submit(pmsp_ctx* c, const pmsp_request* q, uint64_t* ticket) {
     r->H = ref.h;
     r->n_phases = 2 + 2 * q->params.iterations;
     r->bytes = (size_t)r->W * r->H * 6 * sizeof(float);
+    r->tiles = (size_t)((r->W + TILE_W - 1) / TILE_W) * ((r->H + TILE_H - 1) / TILE_H);
     if (r->bytes > c->mem_cap) {
         delete r;
         s.stats.rejected++;
