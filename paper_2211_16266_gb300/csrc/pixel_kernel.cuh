@@ -41,9 +41,13 @@ constexpr int MAX_K = 2 * MAX_HALO + 1;
 
 // Resident blocks per SM the batched kernel's register budget is sized for,
 // by its largest view count (its per-view-count variants share one budget).
-// The single-keyframe kernels leave the choice to the compiler: bounding the
-// 6-view sweep to 7 blocks measured 3 % slower than its own 72 registers.
 constexpr int min_blocks_for(int ns) { return ns <= 4 ? 8 : ns <= 6 ? 7 : ns <= 8 ? 6 : ns <= 10 ? 5 : 4; }
+
+// The single-keyframe kernels: up to 6 views the paired cost path fits 72
+// registers (7 blocks of 128 threads per SM); bounding the 6-view sweep from
+// its own 80 registers to 72 measured 2.5 % faster. Larger view counts are
+// left to the compiler.
+constexpr int pixel_min_blocks(int ns) { return ns <= 6 ? 7 : 1; }
 
 struct TileSmem {
     float ref[TILE_ROWS * TILE_PITCH];  // normalised intensities, halo included
@@ -554,7 +558,7 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm,
 }
 
 template <int NS, bool EXACT, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS) pixel_kernel(const __grid_constant__ PixelParams P) {
+__global__ void __launch_bounds__(BLOCK_THREADS, pixel_min_blocks(NS)) pixel_kernel(const __grid_constant__ PixelParams P) {
     __shared__ TileSmem sm;
     process_tile<NS, EXACT, MODE>(P, sm, blockIdx.x * TILE_W, blockIdx.y * TILE_H, P.colour, P.iter);
 }
