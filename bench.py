@@ -39,6 +39,11 @@ WORKLOAD = "equirect PatchMatch densify 1920x960 u8, 6 sources, 11x11 stride 2, 
 # moments 5  ->  55.
 OPS_PER_VIEW_SAMPLE = 55
 FP32_LANES_PER_SM = 128
+# DRAM bytes of one 6-view half-sweep launch at 1920x960 (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the current kernel build:
+# 49,835,008 read + 1,386,240 written). Set to None whenever the kernel changes
+# until it is captured again.
+SWEEP_DRAM_BYTES = 49_835_008 + 1_386_240
 
 
 def _dist():
@@ -221,7 +226,7 @@ def run_gpu(args):
         vs_per_sweep = W * H / 2 * 14 * N_SRC * 36
         achieved = vs_per_sweep / (sweep_ms / 1e3)
         res["roofline"] = dict(bound="alu", achieved=achieved, peak=peak, unit="view-samples/s",
-                               frac=achieved / peak, traffic=None,
+                               frac=achieved / peak, traffic=SWEEP_DRAM_BYTES, traffic_unit="bytes per launch",
                                kernel="pixel_kernel<6, SWEEP> (one half-sweep)",
                                ms_per_launch=sweep_ms,
                                peak_basis=f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {peak_mhz:.0f} MHz / "
