@@ -90,6 +90,8 @@ def _load():
             lib.orc_plane_sweep.argtypes = [P, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
             lib.orc_warp_init.argtypes = [P, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.POINTER(Pose), _dp, _dp,
                                           _dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            lib.orc_median_filter.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double,
+                                              _dp, _dp]
             lib.orc_consistency_filter.argtypes = [
                 ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(Pose), ctypes.c_int,
                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_dp),
@@ -310,3 +312,16 @@ def consistency_filter(depth, pose_r, nbr_depths, nbr_poses, max_px=1.0, min_vie
                                float(max_px), int(min_views), _ptr(out),
                                agree.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(margin))
     return out, agree, margin
+
+
+def median_filter(depth, radius=2, tau=0.05):
+    """Median post-filter (Sec. III-C, item 2). Returns (filtered depth, window median)."""
+    lib = _load()
+    depth = np.ascontiguousarray(depth, dtype=np.float64)
+    H, W = depth.shape
+    if not 0 <= radius <= 16:
+        raise ValueError("radius must be in [0, 16]")
+    out = np.zeros_like(depth)
+    med = np.zeros_like(depth)
+    lib.orc_median_filter(W, H, _ptr(depth), int(radius), float(tau), _ptr(out), _ptr(med))
+    return out, med

@@ -18,7 +18,9 @@
  *     Fig. 5);
  *   - six random refinement tests on a shrinking search range (Sec. III-C,
  *     item 1);
- *   - consistency filter over neighbouring depth maps (Sec. III).
+ *   - consistency filter over neighbouring depth maps (Sec. III);
+ *   - initialisation by plane-map warping (Sec. III-B);
+ *   - median post-filter of the depth map (Sec. III-C, item 2).
  * Precision: double throughout. Random numbers: Philox4x64-10 (Salmon,
  * Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11).
  * The matching cost (bilaterally weighted NCC, best-k view aggregation) is
@@ -572,4 +574,54 @@ void orc_warp_init(const orc_problem* pb, int Wp, int Hp, const double* prev_dep
             if (clear) clear[i] = clr;
         }
     free(best); free(second); free(who); free(ok);
+}
+
+/* ------------------------------------------------------ median post-filter */
+
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Median post-filter (Sec. III-C, item 2: a median filter runs over a copy of
+ * the depth image and depths that deviate from the filtered copy by more than
+ * a threshold are removed; window and threshold are not given, so this
+ * follows the project's reading). For a pixel with range d > 0, the valid
+ * ranges (> 0) of the (2r+1) x (2r+1) window around it (columns wrapped at
+ * the seam, rows outside the panorama left out) are sorted and the lower
+ * median m, the element of rank floor((n-1)/2), is taken. The range is
+ * removed (set to 0) when |d - m| > tau * m, decided in single precision as
+ * the depth maps are stored. Every decision reads the unfiltered input.
+ * `med` (nullable) receives m (0 where d <= 0).
+ */
+void orc_median_filter(int W, int H, const double* depth, int r, double tau, double* out, double* med) {
+    const float tau32 = (float)tau;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int v = 0; v < H; ++v) {
+        double win[(2 * 16 + 1) * (2 * 16 + 1)];
+        for (int u = 0; u < W; ++u) {
+            size_t i = (size_t)v * W + u;
+            double d = depth[i], m = 0.0;
+            if (d > 0) {
+                int n = 0;
+                for (int dy = -r; dy <= r; ++dy) {
+                    int y = v + dy;
+                    if (y < 0 || y >= H) continue;
+                    for (int dx = -r; dx <= r; ++dx) {
+                        double x = depth[(size_t)y * W + wrap_i(u + dx, W)];
+                        if (x > 0) win[n++] = x;
+                    }
+                }
+                qsort(win, (size_t)n, sizeof(double), cmp_double);
+                m = win[(n - 1) / 2];
+                float d32 = (float)d, m32 = (float)m;
+                float diff = fabsf(d32 - m32), lim = tau32 * m32;
+                out[i] = diff > lim ? 0.0 : d;
+            } else {
+                out[i] = 0.0;
+            }
+            if (med) med[i] = m;
+        }
+    }
 }
