@@ -214,6 +214,24 @@ int pmsp_consistency_filter(pmsp_ctx* ctx, const pmsp_maps* ref, const pmsp_pose
                             int32_t* agree);
 
 /*
+ * Median post-filter (Sec. III-C, item 2: a median filter over a copy of the
+ * depth image; ranges deviating from it by more than a threshold are removed).
+ * For a pixel with range d > 0, the valid ranges (> 0) of its
+ * (2 radius + 1)^2 window (columns wrapped at the seam, rows outside the
+ * panorama left out) give the lower median m (rank floor((n-1)/2)); the
+ * output is 0 where |d - m| > tau * m (FP32), else d. Pixels with d <= 0
+ * output 0. Selection is exact.
+ *   in       depth read (in->depth, w x h)
+ *   radius   1, 2 (5 x 5, the default reading) or 3
+ *   tau      relative threshold > 0 (0.05 in the default reading)
+ *   out      depth written; same size and memory kind as in; must not
+ *            alias in->depth (every decision reads the unfiltered map)
+ * Errors: PMSP_EINVAL for NULL or mismatched maps, aliasing, radius outside
+ * [1, 3] or tau <= 0.
+ */
+int pmsp_median_filter(pmsp_ctx* ctx, const pmsp_maps* in, int radius, float tau, pmsp_maps* out);
+
+/*
  * Bilinear sample of img at n continuous pixel coordinates (integers are pixel
  * centres; longitude wrapped, latitude clamped), the source fetch the cost uses.
  * uc, vc, out: n floats each, in the memory kind of img.

@@ -121,6 +121,7 @@ _SIGS["pmsp_densify_batch_noalloc"] = ([_P, ctypes.POINTER(pmsp_batch_item), cty
 PMSP_NOALLOC_MAX_ITEMS = 16
 _SIGS["pmsp_warp_init"] = ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M, _O, _M, _F], ctypes.c_int)
 _SIGS["pmsp_densify_warped"] = ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M, _O, _M], ctypes.c_int)
+_SIGS["pmsp_median_filter"] = ([_P, _M, ctypes.c_int, ctypes.c_float, _M], ctypes.c_int)
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.argtypes = _args
@@ -397,6 +398,22 @@ def pmsp_consistency_filter(ctx, depth, pose, nbr_depths, nbr_poses, max_px=1.0,
     ctx.check(_lib.pmsp_consistency_filter(ctx.h, ctypes.byref(ref), ctypes.byref(make_pose(pose)), nb, poses,
                                            n, float(max_px), int(min_views), ctypes.byref(o), _ptr(agree)))
     return out, agree
+
+
+def pmsp_median_filter(ctx, depth, radius=2, tau=0.05, out=None):
+    """Median post-filter of `depth` (H, W) (Sec. III-C, item 2); returns the filtered depth."""
+    if _is_torch(depth):
+        import torch
+        out = torch.empty_like(depth) if out is None else out
+    else:
+        depth = np.ascontiguousarray(depth, dtype=np.float32)
+        out = np.zeros_like(depth) if out is None else out
+    H, W = depth.shape
+    mem = PMSP_DEVICE if _is_torch(depth) and depth.is_cuda else PMSP_HOST
+    src = pmsp_maps(W, H, mem, _ptr(depth), None, None)
+    dst = pmsp_maps(W, H, mem, _ptr(out), None, None)
+    ctx.check(_lib.pmsp_median_filter(ctx.h, ctypes.byref(src), int(radius), float(tau), ctypes.byref(dst)))
+    return out
 
 
 def pmsp_sample_bilinear(ctx, img, uc, vc):

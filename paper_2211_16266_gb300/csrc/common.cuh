@@ -121,6 +121,8 @@ template <int MAXS>
 cudaError_t launch_batch_kernel_t(const BatchArgs& a, int grid, cudaStream_t stream);
 cudaError_t launch_pixel_kernel(const PixelParams& p, int mode, cudaStream_t stream);
 cudaError_t launch_filter_kernel(const FilterParams& p, cudaStream_t stream);
+cudaError_t launch_median_kernel(const float* in, float* out, int W, int H, int radius, float tau,
+                                 cudaStream_t stream);
 cudaError_t launch_warp_init(const PixelParams& p, const WarpArgs& a, cudaStream_t stream);
 cudaError_t launch_project_kernel(int W, int H, int n, const float* dirs, float* uc, float* vc,
                                   cudaStream_t stream);

@@ -393,8 +393,8 @@ int pmsp_destroy(pmsp_ctx* c) {
     runtime_shutdown(c);
     for (auto& t : c->src_tex) free_texture(t);
     free_texture(c->sample_tex);
-    for (DevBuffer* b : {&c->ref_stage, &c->map_stage, &c->filter_stage, &c->sample_stage, &c->warp_zbuf,
-                         &c->warp_prev})
+    for (DevBuffer* b : {&c->ref_stage, &c->map_stage, &c->filter_stage, &c->sample_stage, &c->median_stage,
+                         &c->warp_zbuf, &c->warp_prev})
         if (b->ptr) cudaFree(b->ptr);
     if (c->d_err) cudaFree(c->d_err);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -657,6 +657,42 @@ int pmsp_consistency_filter(pmsp_ctx* c, const pmsp_maps* ref, const pmsp_pose* 
         if (e == cudaSuccess && agree)
             e = cudaMemcpyAsync(agree, F.agree, N * 4, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "filter download");
+        return pmsp_sync(c);
+    }
+    return PMSP_OK;
+}
+
+int pmsp_median_filter(pmsp_ctx* c, const pmsp_maps* in, int radius, float tau, pmsp_maps* out) {
+    if (!c) return PMSP_EINVAL;
+    cudaSetDevice(c->device);
+    if (!in || !in->depth || !out || !out->depth) return ctx_fail(c, PMSP_EINVAL, "NULL input or output depth");
+    const int W = in->w, H = in->h;
+    if (W < 1 || H < 1 || out->w != W || out->h != H || out->memory != in->memory)
+        return ctx_fail(c, PMSP_EINVAL, "output must match the input size and memory kind");
+    if (in->memory != PMSP_HOST && in->memory != PMSP_DEVICE) return ctx_fail(c, PMSP_EINVAL, "bad memory kind");
+    if (out->depth == in->depth) return ctx_fail(c, PMSP_EINVAL, "output must not alias the input");
+    if (radius < 1 || radius > 3) return ctx_fail(c, PMSP_EINVAL, "radius %d outside [1, 3]", radius);
+    if (!(tau > 0.f)) return ctx_fail(c, PMSP_EINVAL, "tau must be > 0");
+    const size_t bytes = (size_t)W * H * sizeof(float);
+    const float* din = in->depth;
+    float* dout = out->depth;
+    int rc;
+    const bool host = in->memory == PMSP_HOST;
+    if (host) {
+        const size_t half = (bytes + 255) & ~size_t(255);
+        if ((rc = ensure_buffer(c, c->median_stage, 2 * half))) return rc;
+        float* a = static_cast<float*>(c->median_stage.ptr);
+        float* b = reinterpret_cast<float*>(static_cast<char*>(c->median_stage.ptr) + half);
+        cudaError_t e = cudaMemcpyAsync(a, in->depth, bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "median upload");
+        din = a;
+        dout = b;
+    }
+    cudaError_t e = launch_median_kernel(din, dout, W, H, radius, tau, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "median launch");
+    if (host) {
+        e = cudaMemcpyAsync(out->depth, dout, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "median download");
         return pmsp_sync(c);
     }
     return PMSP_OK;

@@ -60,7 +60,7 @@ struct pmsp_ctx {
     int max_active = 0;
     std::vector<pmsp::TexImage> src_tex;  // one texture per source slot
     pmsp::TexImage sample_tex;
-    pmsp::DevBuffer ref_stage, map_stage, filter_stage, sample_stage;
+    pmsp::DevBuffer ref_stage, map_stage, filter_stage, sample_stage, median_stage;
     pmsp::DevBuffer warp_zbuf, warp_prev;  // plane-map warping: claims, staged previous maps
     pmsp::Serving* serving = nullptr;
     pmsp::BatchEngine* batch = nullptr;
