@@ -90,6 +90,10 @@ def _load():
             lib.orc_plane_sweep.argtypes = [P, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
             lib.orc_warp_init.argtypes = [P, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.POINTER(Pose), _dp, _dp,
                                           _dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            lib.orc_view_filter.argtypes = [ctypes.POINTER(Pose), ctypes.POINTER(Pose), _dp, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
+                                            ctypes.POINTER(ctypes.c_int), _dp]
+            lib.orc_view_filter.restype = ctypes.c_int
             lib.orc_median_filter.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double,
                                               _dp, _dp]
             lib.orc_consistency_filter.argtypes = [
@@ -325,3 +329,17 @@ def median_filter(depth, radius=2, tau=0.05):
     med = np.zeros_like(depth)
     lib.orc_median_filter(W, H, _ptr(depth), int(radius), float(tau), _ptr(out), _ptr(med))
     return out, med
+
+
+def view_filter(pose_a, pose_b, points, min_deg=6.0, max_deg=60.0, min_frac=0.2):
+    """View Filter (Sec. III-A, Eq. 1). Returns (accept, share in range, theta in degrees, in-range flags)."""
+    lib = _load()
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+    n = pts.shape[0]
+    theta = np.zeros(n)
+    flags = np.zeros(n, np.int32)
+    frac = ctypes.c_double(0.0)
+    acc = lib.orc_view_filter(ctypes.byref(make_pose(*pose_a)), ctypes.byref(make_pose(*pose_b)), _ptr(pts), n,
+                              float(min_deg), float(max_deg), float(min_frac), _ptr(theta),
+                              flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(frac))
+    return bool(acc), frac.value, theta, flags.astype(bool)

@@ -20,7 +20,8 @@
  *     item 1);
  *   - consistency filter over neighbouring depth maps (Sec. III);
  *   - initialisation by plane-map warping (Sec. III-B);
- *   - median post-filter of the depth map (Sec. III-C, item 2).
+ *   - median post-filter of the depth map (Sec. III-C, item 2);
+ *   - View Filter on sparse points (Sec. III-A, Eq. 1).
  * Precision: double throughout. Random numbers: Philox4x64-10 (Salmon,
  * Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11).
  * The matching cost (bilaterally weighted NCC, best-k view aggregation) is
@@ -624,4 +625,47 @@ void orc_median_filter(int W, int H, const double* depth, int r, double tau, dou
             if (med) med[i] = m;
         }
     }
+}
+
+/* ------------------------------------------------------------- view filter */
+
+/*
+ * View Filter (Sec. III-A, Eq. 1; the equation is garbled in the source and
+ * read as the parallax angle at p between the rays to the two camera
+ * centres): for every sparse point p seen by keyframes A and B,
+ * theta_p = arccos((t_A - p).(t_B - p) / (|t_A - p| |t_B - p|)), with t_K the
+ * camera centre -R^T t of pose K. B is accepted when the share of points with
+ * theta_p in [min_deg, max_deg] exceeds min_frac (6, 60 degrees and 20 % in
+ * the paper). A point at a camera centre has no angle and counts as out of
+ * range. `theta_deg` and `in_range` (nullable) receive the per-point values;
+ * `frac` (nullable) the share. Returns 1 (accept) or 0.
+ */
+int orc_view_filter(const orc_pose* A, const orc_pose* B, const double* pts, int n, double min_deg,
+                    double max_deg, double min_frac, double* theta_deg, int* in_range, double* frac) {
+    double ca[3], cb[3];
+    for (int k = 0; k < 3; ++k) {
+        ca[k] = -(A->R[k] * A->t[0] + A->R[3 + k] * A->t[1] + A->R[6 + k] * A->t[2]);
+        cb[k] = -(B->R[k] * B->t[0] + B->R[3 + k] * B->t[1] + B->R[6 + k] * B->t[2]);
+    }
+    int cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        const double* p = pts + 3 * (size_t)i;
+        double a[3] = {ca[0] - p[0], ca[1] - p[1], ca[2] - p[2]};
+        double b[3] = {cb[0] - p[0], cb[1] - p[1], cb[2] - p[2]};
+        double la = sqrt(dot3(a, a)), lb = sqrt(dot3(b, b));
+        double th = NAN;
+        int ok = 0;
+        if (la > 0 && lb > 0) {
+            double c = dot3(a, b) / (la * lb);
+            c = c > 1 ? 1 : (c < -1 ? -1 : c);
+            th = acos(c) * (180.0 / ORC_PI);
+            ok = th >= min_deg && th <= max_deg;
+        }
+        cnt += ok;
+        if (theta_deg) theta_deg[i] = th;
+        if (in_range) in_range[i] = ok;
+    }
+    double f = n > 0 ? (double)cnt / n : 0.0;
+    if (frac) *frac = f;
+    return f > min_frac;
 }
