@@ -90,6 +90,13 @@ def _load():
             lib.orc_plane_sweep.argtypes = [P, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
             lib.orc_warp_init.argtypes = [P, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.POINTER(Pose), _dp, _dp,
                                           _dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            lib.orc_fuse.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(_dp), ctypes.POINTER(Pose), ctypes.c_double, _dp,
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, _dp]
+            lib.orc_fuse.restype = ctypes.c_int64
+            lib.orc_completeness.argtypes = [_dp, ctypes.c_int64, ctypes.POINTER(Pose), ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int), _dp]
+            lib.orc_completeness.restype = ctypes.c_double
             lib.orc_view_filter.argtypes = [ctypes.POINTER(Pose), ctypes.POINTER(Pose), _dp, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
                                             ctypes.POINTER(ctypes.c_int), _dp]
@@ -343,3 +350,33 @@ def view_filter(pose_a, pose_b, points, min_deg=6.0, max_deg=60.0, min_frac=0.2)
                               float(min_deg), float(max_deg), float(min_frac), _ptr(theta),
                               flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(frac))
     return bool(acc), frac.value, theta, flags.astype(bool)
+
+
+def fuse(depths, poses, voxel=0.02):
+    """Point-cloud fusion (Sec. III). Returns (points (m, 3) in key order, sources k << 32 | pixel,
+    per-input-pixel voxel-face margin, -1 where there is no point)."""
+    lib = _load()
+    Ds = [np.ascontiguousarray(d, dtype=np.float64) for d in depths]
+    n = len(Ds)
+    Ws = (ctypes.c_int * max(1, n))(*[d.shape[1] for d in Ds])
+    Hs = (ctypes.c_int * max(1, n))(*[d.shape[0] for d in Ds])
+    Dp = (_dp * max(1, n))(*[_ptr(d) for d in Ds])
+    Ps = (Pose * max(1, n))(*[make_pose(R, t) for (R, t) in poses])
+    total = sum(d.size for d in Ds)
+    pts = np.zeros((max(1, total), 3))
+    src = np.zeros(max(1, total), np.int64)
+    margin = np.zeros(max(1, total))
+    m = lib.orc_fuse(n, Ws, Hs, Dp, Ps, float(voxel), _ptr(pts), src.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                     total, _ptr(margin))
+    return pts[:m], src[:m], margin[:total]
+
+
+def completeness(points, pose, W=720, H=360):
+    """Keyframe completeness (Sec. IV). Returns (share of pixels hit, hit flags (H, W), per-point margin)."""
+    lib = _load()
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+    hit = np.zeros((H, W), np.int32)
+    margin = np.zeros(max(1, len(pts)))
+    c = lib.orc_completeness(_ptr(pts), len(pts), ctypes.byref(make_pose(*pose)), int(W), int(H),
+                             hit.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(margin))
+    return c, hit.astype(bool), margin[:len(pts)]

@@ -21,7 +21,8 @@
  *   - consistency filter over neighbouring depth maps (Sec. III);
  *   - initialisation by plane-map warping (Sec. III-B);
  *   - median post-filter of the depth map (Sec. III-C, item 2);
- *   - View Filter on sparse points (Sec. III-A, Eq. 1).
+ *   - View Filter on sparse points (Sec. III-A, Eq. 1);
+ *   - dense point-cloud fusion (Sec. III) and keyframe completeness (Sec. IV).
  * Precision: double throughout. Random numbers: Philox4x64-10 (Salmon,
  * Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11).
  * The matching cost (bilaterally weighted NCC, best-k view aggregation) is
@@ -668,4 +669,115 @@ int orc_view_filter(const orc_pose* A, const orc_pose* B, const double* pts, int
     double f = n > 0 ? (double)cnt / n : 0.0;
     if (frac) *frac = f;
     return f > min_frac;
+}
+
+/* ------------------------------------------ point-cloud fusion, completeness */
+
+typedef struct { int64_t k[3]; int64_t order; } orc_vox;
+
+static int cmp_vox(const void* a, const void* b) {
+    const orc_vox *x = (const orc_vox*)a, *y = (const orc_vox*)b;
+    for (int i = 0; i < 3; ++i)
+        if (x->k[i] != y->k[i]) return (x->k[i] > y->k[i]) - (x->k[i] < y->k[i]);
+    return (x->order > y->order) - (x->order < y->order);
+}
+
+/*
+ * Dense point-cloud fusion (Sec. III: the point-cloud thread takes the
+ * filtered depth maps of consecutive keyframes and erases duplicate points;
+ * the duplicate rule is not given, so this follows the project's reading).
+ * Every pixel with range d > 0 of keyframe k becomes the world point
+ * X = R_k^T (d r_p - t_k). Points are binned into cubic voxels of edge
+ * `voxel` (key floor(X / voxel) per axis); of the points in one voxel the
+ * first in (keyframe, pixel index) order is kept. Writes the kept points (3
+ * doubles each) and their sources (k << 32 | pixel) in increasing key order
+ * (x, then y, then z key), at most `cap` of them, and returns how many
+ * voxels are occupied. `margin` (nullable, one per input pixel in keyframe
+ * order, -1 where d <= 0) receives the smallest distance of the point's
+ * coordinates to a voxel face, in voxels.
+ */
+int64_t orc_fuse(int n, const int* Ws, const int* Hs, const double* const* depth, const orc_pose* poses,
+                 double voxel, double* pts, int64_t* src, int64_t cap, double* margin) {
+    int64_t total = 0;
+    for (int k = 0; k < n; ++k) total += (int64_t)Ws[k] * Hs[k];
+    orc_vox* v = (orc_vox*)malloc((size_t)(total > 0 ? total : 1) * sizeof(orc_vox));
+    int64_t m = 0, base = 0;
+    for (int k = 0; k < n; ++k) {
+        const orc_pose* P = &poses[k];
+        for (int i = 0; i < Ws[k] * Hs[k]; ++i) {
+            double d = depth[k][i];
+            if (!(d > 0)) {
+                if (margin) margin[base + i] = -1;
+                continue;
+            }
+            double r[3], Xc[3], X[3];
+            orc_bearing(Ws[k], Hs[k], i % Ws[k], i / Ws[k], r);
+            for (int a = 0; a < 3; ++a) Xc[a] = d * r[a] - P->t[a];
+            for (int a = 0; a < 3; ++a) X[a] = P->R[a] * Xc[0] + P->R[3 + a] * Xc[1] + P->R[6 + a] * Xc[2];
+            double mg = INFINITY;
+            for (int a = 0; a < 3; ++a) {
+                double q = X[a] / voxel, f = floor(q);
+                v[m].k[a] = (int64_t)f;
+                mg = fmin(mg, fmin(q - f, f + 1 - q));
+            }
+            if (margin) margin[base + i] = mg;
+            v[m].order = ((int64_t)k << 32) | i;
+            ++m;
+        }
+        base += (int64_t)Ws[k] * Hs[k];
+    }
+    qsort(v, (size_t)m, sizeof(orc_vox), cmp_vox);
+    int64_t out = 0;
+    for (int64_t j = 0; j < m; ++j) {
+        if (j > 0 && v[j].k[0] == v[j - 1].k[0] && v[j].k[1] == v[j - 1].k[1] && v[j].k[2] == v[j - 1].k[2])
+            continue;
+        if (out < cap) {
+            int k = (int)(v[j].order >> 32), i = (int)(v[j].order & 0xffffffff);
+            const orc_pose* P = &poses[k];
+            double r[3], Xc[3], d = depth[k][i];
+            orc_bearing(Ws[k], Hs[k], i % Ws[k], i / Ws[k], r);
+            for (int a = 0; a < 3; ++a) Xc[a] = d * r[a] - P->t[a];
+            for (int a = 0; a < 3; ++a)
+                pts[3 * out + a] = P->R[a] * Xc[0] + P->R[3 + a] * Xc[1] + P->R[6 + a] * Xc[2];
+            if (src) src[out] = v[j].order;
+        }
+        ++out;
+    }
+    free(v);
+    return out;
+}
+
+/*
+ * Keyframe-related completeness (Sec. IV: at each keyframe position a
+ * panorama is rendered from the point cloud and the share of its pixels onto
+ * which some 3-D point projects is the completeness; 720 x 360 in the paper).
+ * Every point is moved into the camera of `pose` and projected onto the
+ * nearest pixel of a W x H panorama (u wrapped, v clamped); occlusion plays
+ * no part. Returns the share of pixels hit; `hit` (nullable, W*H) receives
+ * the per-pixel flags and `margin` (nullable, one per point) the distance of
+ * the projection to the nearest pixel boundary, in pixels (a point at the
+ * camera centre gets -1 and hits nothing).
+ */
+double orc_completeness(const double* pts, int64_t n, const orc_pose* pose, int W, int H, int* hit,
+                        double* margin) {
+    int* h = hit ? hit : (int*)malloc((size_t)W * H * sizeof(int));
+    memset(h, 0, (size_t)W * H * sizeof(int));
+    for (int64_t i = 0; i < n; ++i) {
+        double Y[3], uc, vc;
+        apply_pose(pose, pts + 3 * i, Y);
+        if (dot3(Y, Y) == 0) {
+            if (margin) margin[i] = -1;
+            continue;
+        }
+        orc_project(W, H, Y, &uc, &vc);
+        double fu = floor(uc + 0.5), fv = floor(vc + 0.5);
+        double mg = 0.5 - fabs(uc - fu);
+        if (fv >= 0 && fv <= H - 1) mg = fmin(mg, 0.5 - fabs(vc - fv));
+        if (margin) margin[i] = mg;
+        h[(size_t)clamp_i((int)fv, 0, H - 1) * W + wrap_i((int)fu, W)] = 1;
+    }
+    int64_t c = 0;
+    for (size_t j = 0; j < (size_t)W * H; ++j) c += h[j];
+    if (!hit) free(h);
+    return (double)c / ((double)W * H);
 }
