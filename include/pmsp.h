@@ -232,6 +232,62 @@ int pmsp_consistency_filter(pmsp_ctx* ctx, const pmsp_maps* ref, const pmsp_pose
 int pmsp_median_filter(pmsp_ctx* ctx, const pmsp_maps* in, int radius, float tau, pmsp_maps* out);
 
 /*
+ * View Filter (Sec. III-A, Eq. 1, read as the parallax angle at a point): for
+ * each of n sparse points p seen by keyframes a and b,
+ * theta_p = arccos((t_a - p).(t_b - p) / (|t_a - p| |t_b - p|)), t_K the camera
+ * centre -R_K^T t_K. Keyframe b is accepted when the share of points with
+ * theta_p in [min_deg, max_deg] exceeds min_frac (6, 60 and 0.2 in the paper).
+ * FP32 on the device; a point at a camera centre counts as out of range.
+ *   points     3n floats (x, y, z per point, world frame) in `memory`
+ *   in_range   optional (NULL) n bytes, same memory kind, receiving 0/1 per point
+ *   accepted   host int32 receiving 1 (accept) or 0
+ *   fraction   optional host double receiving the share in range (0 if n = 0)
+ * Errors: PMSP_EINVAL for NULL arguments, n < 0, or bounds outside
+ * 0 <= min_deg <= max_deg <= 180, 0 <= min_frac <= 1.
+ */
+int pmsp_view_filter(pmsp_ctx* ctx, const pmsp_pose* a, const pmsp_pose* b, const float* points, int64_t n,
+                     int memory, double min_deg, double max_deg, double min_frac, uint8_t* in_range,
+                     int32_t* accepted, double* fraction);
+
+/*
+ * Dense point-cloud fusion (Sec. III: the point-cloud thread erases duplicate
+ * points of the buffered, consistency-filtered keyframes). Every pixel with
+ * range d > 0 of keyframe k becomes X = R_k^T (d r_p - t_k) (FP32); points are
+ * binned into cubic voxels of edge `voxel` metres (key floor(X / voxel) per
+ * axis, at most 2^20 voxels from the origin on each axis) and each occupied
+ * voxel keeps its first point in (keyframe, pixel index) order. Kept points
+ * are written in that order.
+ *   maps     n depth maps (depth read; any sizes), 1 <= n <= PMSP_MAX_SOURCES,
+ *            all of one memory kind
+ *   poses    n world->camera poses
+ *   points   3 * cap floats receiving x, y, z of the first min(count, cap)
+ *            kept points, same memory kind as the maps (may be NULL if cap = 0)
+ *   src      optional (NULL) cap int64 receiving k << 32 | pixel index
+ *   count    host int64 receiving the number of occupied voxels (call with
+ *            cap = 0 to size the output)
+ * Synchronous. Device memory: a hash table of 16 bytes per slot (a power of
+ * two >= twice the input pixels) plus 4 bytes per input pixel, held by the
+ * context between calls. Errors: PMSP_EINVAL for NULL or mismatched
+ * arguments, voxel <= 0, or a point beyond the key range.
+ */
+int pmsp_fuse(pmsp_ctx* ctx, const pmsp_maps* maps, const pmsp_pose* poses, int n, float voxel, float* points,
+              int64_t* src, int64_t cap, int64_t* count);
+
+/*
+ * Keyframe completeness (Sec. IV: the share of pixels of a panorama rendered
+ * at a keyframe position onto which some 3-D point projects; 720 x 360 in the
+ * paper). Each of the n points is moved into the camera of `pose` and
+ * projected onto the nearest pixel of a W x H panorama (u wrapped, v clamped);
+ * occlusion plays no part.
+ *   points        3n floats in `memory`
+ *   hit           optional (NULL) W*H bytes, same memory kind, receiving 0/1
+ *   completeness  host double receiving pixels hit / (W * H)
+ * Synchronous. Errors: PMSP_EINVAL for NULL arguments, n < 0, W or H < 1.
+ */
+int pmsp_completeness(pmsp_ctx* ctx, const float* points, int64_t n, int memory, const pmsp_pose* pose, int W,
+                      int H, uint8_t* hit, double* completeness);
+
+/*
  * Bilinear sample of img at n continuous pixel coordinates (integers are pixel
  * centres; longitude wrapped, latitude clamped), the source fetch the cost uses.
  * uc, vc, out: n floats each, in the memory kind of img.

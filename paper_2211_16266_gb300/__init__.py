@@ -122,6 +122,13 @@ PMSP_NOALLOC_MAX_ITEMS = 16
 _SIGS["pmsp_warp_init"] = ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M, _O, _M, _F], ctypes.c_int)
 _SIGS["pmsp_densify_warped"] = ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M, _O, _M], ctypes.c_int)
 _SIGS["pmsp_median_filter"] = ([_P, _M, ctypes.c_int, ctypes.c_float, _M], ctypes.c_int)
+_SIGS["pmsp_view_filter"] = ([_P, _O, _O, _F, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double, _F, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
+                             ctypes.c_int)
+_SIGS["pmsp_fuse"] = ([_P, _M, _O, ctypes.c_int, ctypes.c_float, _F, _F, ctypes.c_int64,
+                       ctypes.POINTER(ctypes.c_int64)], ctypes.c_int)
+_SIGS["pmsp_completeness"] = ([_P, _F, ctypes.c_int64, ctypes.c_int, _O, ctypes.c_int, ctypes.c_int, _F,
+                               ctypes.POINTER(ctypes.c_double)], ctypes.c_int)
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.argtypes = _args
@@ -414,6 +421,59 @@ def pmsp_median_filter(ctx, depth, radius=2, tau=0.05, out=None):
     dst = pmsp_maps(W, H, mem, _ptr(out), None, None)
     ctx.check(_lib.pmsp_median_filter(ctx.h, ctypes.byref(src), int(radius), float(tau), ctypes.byref(dst)))
     return out
+
+
+def _points(points):
+    if _is_torch(points):
+        return points, (PMSP_DEVICE if points.is_cuda else PMSP_HOST)
+    return np.ascontiguousarray(np.asarray(points, dtype=np.float32).reshape(-1, 3)), PMSP_HOST
+
+
+def pmsp_view_filter(ctx, pose_a, pose_b, points, min_deg=6.0, max_deg=60.0, min_frac=0.2, in_range=None):
+    """View Filter (Sec. III-A, Eq. 1); returns (accepted, share in range, in-range flags or None)."""
+    pts, mem = _points(points)
+    n = int(pts.shape[0])
+    acc = ctypes.c_int32(0)
+    frac = ctypes.c_double(0.0)
+    ctx.check(_lib.pmsp_view_filter(ctx.h, ctypes.byref(make_pose(pose_a)), ctypes.byref(make_pose(pose_b)),
+                                    _ptr(pts), n, mem, float(min_deg), float(max_deg), float(min_frac),
+                                    _ptr(in_range) if in_range is not None else None, ctypes.byref(acc),
+                                    ctypes.byref(frac)))
+    return bool(acc.value), frac.value, in_range
+
+
+def pmsp_fuse(ctx, depths, poses, voxel=0.02, cap=None):
+    """Point-cloud fusion (Sec. III); returns (points (m, 3), sources k << 32 | pixel, count)."""
+    n = len(depths)
+    dev = _is_torch(depths[0]) and depths[0].is_cuda
+    mem = PMSP_DEVICE if dev else PMSP_HOST
+    if not dev:
+        depths = [np.ascontiguousarray(d, dtype=np.float32) for d in depths]
+    maps = (pmsp_maps * n)(*[pmsp_maps(d.shape[1], d.shape[0], mem, _ptr(d), None, None) for d in depths])
+    ps = (pmsp_pose * n)(*[make_pose(p) for p in poses])
+    cnt = ctypes.c_int64(0)
+    if cap is None:
+        ctx.check(_lib.pmsp_fuse(ctx.h, maps, ps, n, float(voxel), None, None, 0, ctypes.byref(cnt)))
+        cap = cnt.value
+    if dev:
+        import torch
+        pts = torch.empty((max(1, cap), 3), dtype=torch.float32, device=depths[0].device)
+        src = torch.empty(max(1, cap), dtype=torch.int64, device=depths[0].device)
+    else:
+        pts = np.zeros((max(1, cap), 3), np.float32)
+        src = np.zeros(max(1, cap), np.int64)
+    ctx.check(_lib.pmsp_fuse(ctx.h, maps, ps, n, float(voxel), _ptr(pts), _ptr(src), int(cap), ctypes.byref(cnt)))
+    m = min(cnt.value, cap)
+    return pts[:m], src[:m], cnt.value
+
+
+def pmsp_completeness(ctx, points, pose, W=720, H=360, hit=None):
+    """Keyframe completeness (Sec. IV); returns (share of pixels hit, hit flags or None)."""
+    pts, mem = _points(points)
+    out = ctypes.c_double(0.0)
+    ctx.check(_lib.pmsp_completeness(ctx.h, _ptr(pts), int(pts.shape[0]), mem, ctypes.byref(make_pose(pose)),
+                                     int(W), int(H), _ptr(hit) if hit is not None else None, ctypes.byref(out)))
+    return out.value, hit
 
 
 def pmsp_sample_bilinear(ctx, img, uc, vc):

@@ -18,11 +18,12 @@ constexpr int MAX_HALO = (PMSP_MAX_PATCH_W - 1) / 2;
 
 // Error bits written to the device error word.
 constexpr unsigned ERR_BAD_INDEX = 1u;
+constexpr unsigned ERR_RANGE = 2u;     // a fused point lies outside the voxel key range
+constexpr unsigned ERR_CAPACITY = 4u;  // a hash table ran out of slots
 
-// One source view as the kernels see it.
-// m[0..11]: rows of the reference->source rigid transform with the
-// translation last (Y_i = m[4i..4i+2] . X + m[4i+3]); m[12..15]: (su, ou, sv, ov)
-// with u_c = lon * su + ou, v_c = lat * sv + ov.
+// One source view as the kernels see it: its texture, the reference->source
+// rotation R (row-major) and translation t, and the projection scales with
+// u_c = lon * su + ou, v_c = lat * sv + ov.
 // 80 bytes; inside PixelParams every view starts on a 16-byte boundary, so the
 // batched kernel can copy it as five 16-byte words. (This field order measured
 // 9 % faster in the single-keyframe kernel than rows-with-translation layouts.)
@@ -104,6 +105,46 @@ struct WarpArgs {
     int* src;                  // optional: winning previous pixel or -1
 };
 
+// One keyframe's depth map and pose for point-cloud fusion.
+struct CloudView {
+    const float* depth;  // W x H ranges, <= 0: no point
+    int W, H;
+    float R[9], t[3];    // world -> camera
+};
+
+constexpr int MAX_FUSE_VIEWS = PMSP_MAX_SOURCES;
+
+struct FuseArgs {
+    CloudView views[MAX_FUSE_VIEWS];
+    long long base[MAX_FUSE_VIEWS];  // offset of each keyframe's pixels in the mark array
+    float inv_voxel;
+    unsigned long long* keys;        // hash table: packed voxel keys, ~0 = empty
+    unsigned long long* vals;        // smallest (keyframe << 32 | pixel) per voxel
+    unsigned long long mask;         // table capacity - 1 (capacity a power of two)
+    float* points;                   // output: 3 floats per kept point
+    long long* src;                  // output (optional): keyframe << 32 | pixel
+    long long cap;                   // output capacity in points
+    unsigned* err;
+};
+
+struct CompletenessArgs {
+    const float* points;  // 3 floats per point, world frame
+    long long n;
+    float R[9], t[3];     // world -> camera
+    int W, H;
+    float su, ou, sv, ov;
+    unsigned char* hit;   // W x H flags
+};
+
+struct ViewFilterArgs {
+    const float* points;  // 3 floats per point, world frame
+    long long n;
+    float ca[3], cb[3];   // camera centres
+    float cos_min, cos_max;  // cos(min angle), cos(max angle)
+    unsigned char* flags;    // optional, n
+    unsigned long long* count;
+};
+
 // Arguments of one launch of the persistent batched kernel.
 struct BatchArgs {
     const PixelParams* problems;  // device array, one per keyframe
@@ -124,6 +165,10 @@ cudaError_t launch_filter_kernel(const FilterParams& p, cudaStream_t stream);
 cudaError_t launch_median_kernel(const float* in, float* out, int W, int H, int radius, float tau,
                                  cudaStream_t stream);
 cudaError_t launch_warp_init(const PixelParams& p, const WarpArgs& a, cudaStream_t stream);
+cudaError_t launch_fuse(const FuseArgs& a, int n, unsigned* mark, unsigned* sums, long long total,
+                        unsigned long long* count, cudaStream_t stream);
+cudaError_t launch_completeness(const CompletenessArgs& a, unsigned long long* count, cudaStream_t stream);
+cudaError_t launch_view_filter(const ViewFilterArgs& a, cudaStream_t stream);
 cudaError_t launch_project_kernel(int W, int H, int n, const float* dirs, float* uc, float* vc,
                                   cudaStream_t stream);
 cudaError_t launch_sample_kernel(cudaTextureObject_t tex, int W, int H, int n, const float* uc,

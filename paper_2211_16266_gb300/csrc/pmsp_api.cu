@@ -394,7 +394,7 @@ int pmsp_destroy(pmsp_ctx* c) {
     for (auto& t : c->src_tex) free_texture(t);
     free_texture(c->sample_tex);
     for (DevBuffer* b : {&c->ref_stage, &c->map_stage, &c->filter_stage, &c->sample_stage, &c->median_stage,
-                         &c->warp_zbuf, &c->warp_prev})
+                         &c->warp_zbuf, &c->warp_prev, &c->cloud_table, &c->cloud_stage})
         if (b->ptr) cudaFree(b->ptr);
     if (c->d_err) cudaFree(c->d_err);
     if (c->own_stream) cudaStreamDestroy(c->stream);

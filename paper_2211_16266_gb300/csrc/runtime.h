@@ -61,6 +61,7 @@ struct pmsp_ctx {
     std::vector<pmsp::TexImage> src_tex;  // one texture per source slot
     pmsp::TexImage sample_tex;
     pmsp::DevBuffer ref_stage, map_stage, filter_stage, sample_stage, median_stage;
+    pmsp::DevBuffer cloud_table, cloud_stage;  // fusion (hash table, marks, staging); view filter, completeness
     pmsp::DevBuffer warp_zbuf, warp_prev;  // plane-map warping: claims, staged previous maps
     pmsp::Serving* serving = nullptr;
     pmsp::BatchEngine* batch = nullptr;
