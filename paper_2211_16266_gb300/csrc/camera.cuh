@@ -70,6 +70,34 @@ __device__ __forceinline__ void project_dir_fast(float X, float Y, float Z, floa
     vc = fmaf(lat, sv, ov);
 }
 
+// 1/x on the special-function unit (rcp.approx: relative error ~2^-23).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The projection of the densification kernels, in half-angle form: both
+// arctangent arguments stay in [-1, 1] with no octant logic.
+// lon = 2 atan(X / (rho + |Z|)) where Z >= 0 and sign(X) pi minus it where
+// Z < 0; -lat = 2 atan(Y / (|Y| + rho)), rho = hypot(X, Z). The 1e-30 terms
+// keep the reciprocals finite on the degenerate axis (the angles are then 0).
+// nsv = -sv. The paired cost path performs exactly these operations per lane.
+__device__ __forceinline__ void project_dir_half(float X, float Y, float Z, float su, float ou, float nsv,
+                                                 float ov, float& uc, float& vc) {
+    const float tiny = 1e-30f;
+    const float q = fmaf(X, X, Z * Z);
+    const float rho = q * rsqrtf(q + tiny);
+    const float ql = X * rcp_approx((rho + fabsf(Z)) + tiny);
+    const float r2 = fmaf(Y, Y, q);
+    const float r3 = r2 * rsqrtf(r2 + tiny);
+    const float qt = Y * rcp_approx((r3 + rho) + tiny);
+    const float al = ql * atan2x_poly(ql * ql), nlat = qt * atan2x_poly(qt * qt);
+    const float lon = Z >= 0.f ? al : copysignf(3.14159265358979324f, X) - al;
+    uc = fmaf(lon, su, ou);
+    vc = fmaf(nlat, nsv, ov);
+}
+
 // floor(x) for |x| < 2^22 with two FP32 adds: adding 1.5 * 2^23 rounded
 // towards -inf leaves floor(x) in the low mantissa bits.
 __device__ __forceinline__ float floor_small(float x) {
@@ -101,35 +129,6 @@ __device__ __forceinline__ float2 pair(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-
-// atan(mn / mx) for two lanes (see atan_reduced).
-__device__ __forceinline__ float2 atan_reduced2(float2 mn, float2 mx) {
-    const float2 r = make_float2(__fdividef(mn.x, fmaxf(mx.x, 1e-30f)), __fdividef(mn.y, fmaxf(mx.y, 1e-30f)));
-    return mul2(r, atan_poly2(mul2(r, r)));
-}
-
-__device__ __forceinline__ float2 fast_atan2_pair(float2 y, float2 x) {
-    const float2 ax = make_float2(fabsf(x.x), fabsf(x.y)), ay = make_float2(fabsf(y.x), fabsf(y.y));
-    float2 a = atan_reduced2(make_float2(fminf(ax.x, ay.x), fminf(ax.y, ay.y)),
-                             make_float2(fmaxf(ax.x, ay.x), fmaxf(ax.y, ay.y)));
-    const float2 b = add2(pair(1.57079632679489662f), make_float2(-a.x, -a.y));
-    a.x = ay.x > ax.x ? b.x : a.x;
-    a.y = ay.y > ax.y ? b.y : a.y;
-    const float2 c = add2(pair(3.14159265358979324f), make_float2(-a.x, -a.y));
-    a.x = x.x < 0.f ? c.x : a.x;
-    a.y = x.y < 0.f ? c.y : a.y;
-    return make_float2(copysignf(a.x, y.x), copysignf(a.y, y.y));
-}
-
-__device__ __forceinline__ float2 fast_atan2_xpos_pair(float2 y, float2 x) {
-    const float2 ay = make_float2(fabsf(y.x), fabsf(y.y));
-    float2 a = atan_reduced2(make_float2(fminf(x.x, ay.x), fminf(x.y, ay.y)),
-                             make_float2(fmaxf(x.x, ay.x), fmaxf(x.y, ay.y)));
-    const float2 b = add2(pair(1.57079632679489662f), make_float2(-a.x, -a.y));
-    a.x = ay.x > x.x ? b.x : a.x;
-    a.y = ay.y > x.y ? b.y : a.y;
-    return make_float2(copysignf(a.x, y.x), copysignf(a.y, y.y));
-}
 
 __device__ __forceinline__ float2 floor_small2(float2 x) {
     const float M = 12582912.0f;

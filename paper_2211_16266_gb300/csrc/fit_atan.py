@@ -118,14 +118,24 @@ def main():
             for ck in reversed(c[:-1]):
                 f.write(f"    p = fmaf(p, s, {float(np.float32(ck))!r}f);\n")
             f.write("    return p;\n}\n\n")
-            f.write("// The same polynomial on two lanes with packed FP32 FMAs.\n")
-            f.write("__device__ __forceinline__ float2 atan_poly2(float2 s) {\n")
-            v = float(np.float32(c[-1]))
-            f.write(f"    float2 p = make_float2({v!r}f, {v!r}f);\n")
+            f.write("// 2 P(s): 2 atan(q) = q * 2 P(q^2) for |q| <= 1 (coefficients doubled, which is exact).\n")
+            f.write("__device__ __forceinline__ float atan2x_poly(float s) {\n")
+            f.write(f"    float p = {float(np.float32(2 * c[-1]))!r}f;\n")
             for ck in reversed(c[:-1]):
-                v = float(np.float32(ck))
-                f.write(f"    p = __ffma2_rn(p, s, make_float2({v!r}f, {v!r}f));\n")
-            f.write("    return p;\n}\n\n}  // namespace pmsp\n")
+                f.write(f"    p = fmaf(p, s, {float(np.float32(2 * ck))!r}f);\n")
+            f.write("    return p;\n}\n\n")
+            f.write("// 2 P(s) for two pairs of lanes at once, packed FP32 FMAs interleaved so each\n")
+            f.write("// coefficient pair serves both: 2 atan(q) = q * 2 P(q^2) for |q| <= 1, the form\n")
+            f.write("// the paired projection uses (coefficients doubled, which is exact).\n")
+            f.write("__device__ __forceinline__ void atan2x_poly2_dual(float2 s1, float2 s2, float2& p1, float2& p2) {\n")
+            v = float(np.float32(2 * c[-1]))
+            f.write(f"    p1 = make_float2({v!r}f, {v!r}f);\n")
+            f.write("    p2 = p1;\n")
+            for ck in reversed(c[:-1]):
+                v = float(np.float32(2 * ck))
+                f.write(f"    p1 = __ffma2_rn(p1, s1, make_float2({v!r}f, {v!r}f));\n")
+                f.write(f"    p2 = __ffma2_rn(p2, s2, make_float2({v!r}f, {v!r}f));\n")
+            f.write("}\n\n}  // namespace pmsp\n")
         print("wrote", path)
 
 

@@ -66,7 +66,7 @@ __device__ __forceinline__ float view_sample<LinearViews>(const SourceView& V, f
     const float Yy = fmaf(V.R[3], X, fmaf(V.R[4], Y, fmaf(V.R[5], Z, V.t[1])));
     const float Yz = fmaf(V.R[6], X, fmaf(V.R[7], Y, fmaf(V.R[8], Z, V.t[2])));
     float uc, vc;
-    project_dir_fast(Yx, Yy, Yz, V.su, V.ou, V.sv, V.ov, uc, vc);
+    project_dir_half(Yx, Yy, Yz, V.su, V.ou, -V.sv, V.ov, uc, vc);
     const LinearSrc& L = na_lin[s];
     const float fi = floor_small(uc), fj = floor_small(vc);
     const float fx = uc - fi, fy = vc - fj;

@@ -208,7 +208,7 @@ __device__ __forceinline__ float view_sample(const SourceView& V, float X, float
     const float Yy = fmaf(L.r(3), X, fmaf(L.r(4), Y, fmaf(L.r(5), Z, L.t(1))));
     const float Yz = fmaf(L.r(6), X, fmaf(L.r(7), Y, fmaf(L.r(8), Z, L.t(2))));
     float uc, vc;
-    project_dir_fast(Yx, Yy, Yz, L.su(), L.ou(), L.sv(), L.ov(), uc, vc);
+    project_dir_half(Yx, Yy, Yz, L.su(), L.ou(), -L.sv(), L.ov(), uc, vc);
     return sample_bilinear(L.tex(), L.inv_w(), L.inv_h(), uc, vc);
 }
 
@@ -319,11 +319,27 @@ __device__ __forceinline__ float2 pair_sample(const PixelParams::ViewPair& VP, c
     const float2 Yx = fma2(VP.R[0], Xv, fma2(VP.R[1], Yv, fma2(VP.R[2], Zv, VP.t[0])));
     const float2 Yy = fma2(VP.R[3], Xv, fma2(VP.R[4], Yv, fma2(VP.R[5], Zv, VP.t[1])));
     const float2 Yz = fma2(VP.R[6], Xv, fma2(VP.R[7], Yv, fma2(VP.R[8], Zv, VP.t[2])));
-    const float2 lon = fast_atan2_pair(Yx, Yz);
+    // Half-angle forms keep the arctangent argument in [-1, 1] with no octant
+    // logic: lon = 2 atan(x / (rho + |z|)) where z >= 0 and sign(x) pi minus it
+    // where z < 0; -lat = 2 atan(y / (|Y| + rho)). The 1e-30 terms keep the
+    // reciprocals finite on the degenerate axis (the angles are then 0).
+    const float2 tiny = pair(1e-30f);
     const float2 q = fma2(Yx, Yx, mul2(Yz, Yz));
-    const float2 rho = mul2(q, make_float2(rsqrtf(fmaxf(q.x, 1e-30f)), rsqrtf(fmaxf(q.y, 1e-30f))));
-    const float2 lat = fast_atan2_xpos_pair(make_float2(-Yy.x, -Yy.y), rho);
-    const float2 uc = fma2(lon, VP.su, VP.ou), vc = fma2(lat, VP.sv, VP.ov);
+    const float2 qa = add2(q, tiny);
+    const float2 rho = mul2(q, make_float2(rsqrtf(qa.x), rsqrtf(qa.y)));
+    const float2 dl = add2(add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y))), tiny);
+    const float2 ql = mul2(Yx, make_float2(rcp_approx(dl.x), rcp_approx(dl.y)));
+    const float2 r2 = fma2(Yy, Yy, q);
+    const float2 r2a = add2(r2, tiny);
+    const float2 r3 = mul2(r2, make_float2(rsqrtf(r2a.x), rsqrtf(r2a.y)));
+    const float2 dt = add2(add2(r3, rho), tiny);
+    const float2 qt = mul2(Yy, make_float2(rcp_approx(dt.x), rcp_approx(dt.y)));
+    float2 pl, pt;
+    atan2x_poly2_dual(mul2(ql, ql), mul2(qt, qt), pl, pt);
+    const float2 al = mul2(ql, pl), nlat = mul2(qt, pt);
+    const float2 lon = make_float2(Yz.x >= 0.f ? al.x : copysignf(3.14159265358979324f, Yx.x) - al.x,
+                                   Yz.y >= 0.f ? al.y : copysignf(3.14159265358979324f, Yx.y) - al.y);
+    const float2 uc = fma2(lon, VP.su, VP.ou), vc = fma2(nlat, VP.nsv, VP.ov);
     const float2 fi = floor_small2(uc), fj = floor_small2(vc);
     const float2 fx = add2(uc, make_float2(-fi.x, -fi.y)), fy = add2(vc, make_float2(-fj.x, -fj.y));
     const float2 xn = fma2(fi, VP.inv_w, VP.inv_w), yn = fma2(fj, VP.inv_h, VP.inv_h);

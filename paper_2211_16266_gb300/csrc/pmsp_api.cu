@@ -251,7 +251,7 @@ void fill_problem(PixelParams& P, const pmsp_image* ref, const void* ref_dev, in
         for (int k = 0; k < 3; ++k) VP.t[k] = make_float2(A.t[k], B.t[k]);
         VP.su = make_float2(A.su, B.su);
         VP.ou = make_float2(A.ou, B.ou);
-        VP.sv = make_float2(A.sv, B.sv);
+        VP.nsv = make_float2(-A.sv, -B.sv);
         VP.ov = make_float2(A.ov, B.ov);
         VP.inv_w = make_float2(A.inv_w, B.inv_w);
         VP.inv_h = make_float2(A.inv_h, B.inv_h);
