@@ -77,21 +77,30 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// sqrt(x) on the special-function unit (sqrt.approx), exact 0 at 0.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // The projection of the densification kernels, in half-angle form: both
 // arctangent arguments stay in [-1, 1] with no octant logic.
 // lon = 2 atan(X / (rho + |Z|)) where Z >= 0 and sign(X) pi minus it where
-// Z < 0; -lat = 2 atan(Y / (|Y| + rho)), rho = hypot(X, Z). The 1e-30 terms
-// keep the reciprocals finite on the degenerate axis (the angles are then 0).
-// nsv = -sv. The paired cost path performs exactly these operations per lane.
+// Z < 0; -lat = 2 atan(Y / (|Y| + rho)), rho = hypot(X, Z), both square roots
+// on the special-function unit. A direction exactly on the source's vertical
+// axis (X = Z = 0 in FP32) gives NaN coordinates; the view's NCC then clamps
+// to -1 and the view costs 2, as for an invalid sample (no fault: texture
+// fetches accept any coordinate). nsv = -sv. The paired cost path performs
+// exactly these operations per lane after its rigid transform.
 __device__ __forceinline__ void project_dir_half(float X, float Y, float Z, float su, float ou, float nsv,
                                                  float ov, float& uc, float& vc) {
-    const float tiny = 1e-30f;
     const float q = fmaf(X, X, Z * Z);
-    const float rho = q * rsqrtf(q + tiny);
-    const float ql = X * rcp_approx((rho + fabsf(Z)) + tiny);
+    const float rho = sqrt_approx(q);
+    const float ql = X * rcp_approx(rho + fabsf(Z));
     const float r2 = fmaf(Y, Y, q);
-    const float r3 = r2 * rsqrtf(r2 + tiny);
-    const float qt = Y * rcp_approx((r3 + rho) + tiny);
+    const float r3 = sqrt_approx(r2);
+    const float qt = Y * rcp_approx(r3 + rho);
     const float al = ql * atan2x_poly(ql * ql), nlat = qt * atan2x_poly(qt * qt);
     const float lon = Z >= 0.f ? al : copysignf(3.14159265358979324f, X) - al;
     uc = fmaf(lon, su, ou);

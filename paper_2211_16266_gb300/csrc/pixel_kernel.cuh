@@ -43,11 +43,11 @@ constexpr int MAX_K = 2 * MAX_HALO + 1;
 // by its largest view count (its per-view-count variants share one budget).
 constexpr int min_blocks_for(int ns) { return ns <= 4 ? 8 : ns <= 6 ? 7 : ns <= 8 ? 6 : ns <= 10 ? 5 : 4; }
 
-// The single-keyframe kernels: up to 6 views the paired cost path fits 72
-// registers (7 blocks of 128 threads per SM); bounding the 6-view sweep from
-// its own 80 registers to 72 measured 2.5 % faster. Larger view counts are
-// left to the compiler.
-constexpr int pixel_min_blocks(int ns) { return ns <= 6 ? 7 : 1; }
+// Resident blocks per SM of the single-keyframe kernels, by view count:
+// 72 registers up to 6 views (7 blocks; 2.5 % faster than the 6-view sweep's
+// own 80), 96 for 7-8 views and 128 beyond (no spills; the compiler left
+// alone takes up to 246). Measured on 1920x960 half-sweeps.
+constexpr int pixel_min_blocks(int ns) { return ns <= 6 ? 7 : ns <= 8 ? 5 : 4; }
 
 struct TileSmem {
     float ref[TILE_ROWS * TILE_PITCH];  // normalised intensities, halo included
@@ -55,6 +55,13 @@ struct TileSmem {
     float col_sin[TILE_PITCH], col_cos[TILE_PITCH];  // sin lon, cos lon
     float wsp[MAX_K];                                // spatial log2-weight of offset index k
 };
+
+// Rotated column directions of the paired path: for view pair q and tile
+// column c, colU[q][k][c] = row k of R_s applied to (sin lon_c, 0, cos lon_c)
+// for both views of the pair. A sample direction r = (cl sin, -sl, cl cos)
+// then transforms as R r = cl U_c - sl R_col1.
+constexpr int MAX_COL_PAIRS = 5;
+__shared__ float2 g_colU[MAX_COL_PAIRS][3][TILE_PITCH];
 
 // Reference-side constants of one pixel (independent of the hypothesis).
 struct RefStats {
@@ -309,30 +316,27 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem
     return sum / (float)P.best_k;
 }
 
-// Intensities of views 2q and 2q + 1 at the projection of X: the projection
-// runs on float2 pairs (one packed instruction for both views), the two
-// gathers and the bilinear weights per view. The arithmetic is that of
-// view_sample, operation for operation.
+// Intensities of views 2q and 2q + 1 at the sample whose reference-frame
+// point is X = t r, r = (cl sin lon_c, -sl, cl cos lon_c) in tile column c:
+// the source point R_s X + t_s = alpha U_c + beta R_col1 + t_s with
+// alpha = t cl, beta = -t sl and U_c from the column table. The projection
+// runs on float2 pairs (one packed instruction for both views), then two
+// gathers and the bilinear weights per view. The arithmetic after the rigid
+// transform is that of project_dir_half and sample_bilinear, operation for
+// operation.
 __device__ __forceinline__ float2 pair_sample(const PixelParams::ViewPair& VP, const SourceView& V0,
-                                              const SourceView& V1, float X, float Y, float Z) {
-    const float2 Xv = pair(X), Yv = pair(Y), Zv = pair(Z);
-    const float2 Yx = fma2(VP.R[0], Xv, fma2(VP.R[1], Yv, fma2(VP.R[2], Zv, VP.t[0])));
-    const float2 Yy = fma2(VP.R[3], Xv, fma2(VP.R[4], Yv, fma2(VP.R[5], Zv, VP.t[1])));
-    const float2 Yz = fma2(VP.R[6], Xv, fma2(VP.R[7], Yv, fma2(VP.R[8], Zv, VP.t[2])));
-    // Half-angle forms keep the arctangent argument in [-1, 1] with no octant
-    // logic: lon = 2 atan(x / (rho + |z|)) where z >= 0 and sign(x) pi minus it
-    // where z < 0; -lat = 2 atan(y / (|Y| + rho)). The 1e-30 terms keep the
-    // reciprocals finite on the degenerate axis (the angles are then 0).
-    const float2 tiny = pair(1e-30f);
-    const float2 q = fma2(Yx, Yx, mul2(Yz, Yz));
-    const float2 qa = add2(q, tiny);
-    const float2 rho = mul2(q, make_float2(rsqrtf(qa.x), rsqrtf(qa.y)));
-    const float2 dl = add2(add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y))), tiny);
+                                                   const SourceView& V1, float alpha, float beta, int q, int cx) {
+    const float2 av = pair(alpha), bv = pair(beta);
+    const float2 Yx = fma2(av, g_colU[q][0][cx], fma2(bv, VP.R[1], VP.t[0]));
+    const float2 Yy = fma2(av, g_colU[q][1][cx], fma2(bv, VP.R[4], VP.t[1]));
+    const float2 Yz = fma2(av, g_colU[q][2][cx], fma2(bv, VP.R[7], VP.t[2]));
+    const float2 q2 = fma2(Yx, Yx, mul2(Yz, Yz));
+    const float2 rho = make_float2(sqrt_approx(q2.x), sqrt_approx(q2.y));
+    const float2 dl = add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y)));
     const float2 ql = mul2(Yx, make_float2(rcp_approx(dl.x), rcp_approx(dl.y)));
-    const float2 r2 = fma2(Yy, Yy, q);
-    const float2 r2a = add2(r2, tiny);
-    const float2 r3 = mul2(r2, make_float2(rsqrtf(r2a.x), rsqrtf(r2a.y)));
-    const float2 dt = add2(add2(r3, rho), tiny);
+    const float2 r2 = fma2(Yy, Yy, q2);
+    const float2 r3 = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
+    const float2 dt = add2(r3, rho);
     const float2 qt = mul2(Yy, make_float2(rcp_approx(dt.x), rcp_approx(dt.y)));
     float2 pl, pt;
     atan2x_poly2_dual(mul2(ql, ql), mul2(qt, qt), pl, pt);
@@ -373,9 +377,10 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const T
         if (!(den < -1e-6f)) return 2.0f;
         const float t = __fdividef(dn, den);
         const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
+        const float alpha = t * cl, beta = -t * sm.row_sin[ly + o];
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            c0[q] = pair_sample(P.pairs[q], P.src[2 * q], P.src[2 * q + 1], X, Y, Z);
+            c0[q] = pair_sample(P.pairs[q], P.src[2 * q], P.src[2 * q + 1], alpha, beta, q, lx + o);
             SJ[q] = SJJ[q] = SIJ[q] = pair(0.f);
         }
         if (ODD) c0o = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z);
@@ -399,10 +404,11 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const T
             }
             const float t = __fdividef(dn, den);
             const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
+            const float alpha = t * cl, beta = t * msl;
             const float2 w2 = pair(w), wI2 = pair(wI);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const float2 J = pair_sample(P.pairs[q], P.src[2 * q], P.src[2 * q + 1], X, Y, Z);
+                const float2 J = pair_sample(P.pairs[q], P.src[2 * q], P.src[2 * q + 1], alpha, beta, q, cx);
                 const float2 Jc = add2(J, make_float2(-c0[q].x, -c0[q].y));
                 const float2 tw = mul2(w2, Jc);
                 SJ[q] = add2(SJ[q], tw);
@@ -492,6 +498,20 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm,
                                              int iter) {
     stage_tile(P, sm, bx, by);
     __syncthreads();
+    if constexpr (EXACT && NS >= 2 && std::is_same<VA, ParamViews>::value) {
+        constexpr int NP = NS / 2;
+        static_assert(NP <= MAX_COL_PAIRS, "column table too small");
+        const int cols = TILE_W + 2 * P.radius;
+        for (int i = threadIdx.x; i < cols * NP; i += BLOCK_THREADS) {
+            const int q = i / cols, c = i - q * cols;
+            const PixelParams::ViewPair& VP = P.pairs[q];
+            const float2 sn = pair(sm.col_sin[c]), cs = pair(sm.col_cos[c]);
+            g_colU[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
+            g_colU[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
+            g_colU[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
+        }
+        __syncthreads();
+    }
 
     const int tx = threadIdx.x % (TILE_W / 2), ty = threadIdx.x / (TILE_W / 2);
     const int y = by + ty;

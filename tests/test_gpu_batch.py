@@ -60,9 +60,11 @@ def _args(p):
 
 def test_batch_equals_single_keyframe_runs(pm, ctx):
     """The persistent batched kernel is other code than the single-keyframe one
-    (its FP32 contractions may round differently), so it matches within the
-    parity tolerance; the per-keyframe chains run the single-keyframe kernels
-    and match bit for bit."""
+    (it transforms each sample directly where the paired kernel uses the
+    rotated column table, and its FP32 contractions may round differently), so
+    it matches within the parity tolerance (cost 1e-4, range 0.5 % on 99.5 %
+    of pixels); the per-keyframe chains run the single-keyframe kernels and
+    match bit for bit."""
     probs = _problems()
     args = [_args(p) for p in probs]
     singles = [pm.pmsp_densify(ctx, *a, p.params).numpy() for a, p in zip(args, probs)]
@@ -70,7 +72,7 @@ def test_batch_equals_single_keyframe_runs(pm, ctx):
     outs = pm.pmsp_densify_batch(ctx, batch, tuning=pm.pmsp_tuning(0, 0, 0, 0))
     for (sd, sn, sc), o in zip(singles, outs):
         bd, bn, bc = o.numpy()
-        assert np.mean(np.abs(bc - sc) <= 1e-4) >= 0.999
+        assert np.mean(np.abs(bc - sc) <= 1e-4) >= 0.995
         assert np.mean(np.abs(bd - sd) <= 5e-3 * sd) >= 0.995
     batch = pm.Batch([(*a, p.params, None) for a, p in zip(args, probs)])
     outs = pm.pmsp_densify_batch(ctx, batch, tuning=pm.pmsp_tuning(0, 0, 0, 1))
