@@ -104,6 +104,24 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+def max_over_ranks(x: float) -> float:
+    """Largest value of x over the ranks of the (gloo) process group; every rank
+    gets it. Replicas run independent keyframes, so this timing reduction is the
+    only exchange between them."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(world_size: int, steps: int, max_total_ms: float) -> float:
+    """Whole-job keyframes/s of N replicas: every rank densifies `steps` keyframes,
+    the job takes as long as the slowest rank."""
+    return world_size * steps / (max_total_ms / 1e3)
+
+
 def make_workload(seed_scene=1001):
     """Trajectory of 7 + 4 frames: keyframe = frame 5, sources = frames 2..4, 6..8,
     filter neighbours = keyframes 3, 4, 6, 7 (their maps are densified in warm-up)."""
@@ -193,11 +211,7 @@ def run_gpu(args):
     times = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(times)
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms)
 
     # dominant kernel: time the 16 half-sweeps of one keyframe alone (same stream)
     sweep_ms = time_sweeps(pm, ctx, stream, kf_args, params, out, flush)
@@ -209,7 +223,7 @@ def run_gpu(args):
     clocks = clk.summary() or {}
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     res = dict(
-        metric=METRIC, value=ws * args.steps / (total_ms / 1e3), unit="keyframes/s", n_gpus=ws,
+        metric=METRIC, value=replica_throughput(ws, args.steps, total_ms), unit="keyframes/s", n_gpus=ws,
         steps=args.steps, warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="u8 images, f32 math", data="synthetic",
         config=dict(workload=WORKLOAD, width=W, height=H, sources=N_SRC, iterations=ITERS, window="11x11/2",

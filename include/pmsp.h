@@ -123,7 +123,8 @@ int pmsp_create(pmsp_ctx** out, const pmsp_ctx_opts* opts);
 int pmsp_destroy(pmsp_ctx* ctx);
 /* Text of the most recent failure on this context ("" if none). Valid until the next call. */
 const char* pmsp_last_error(pmsp_ctx* ctx);
-/* Block until the context stream is idle; PMSP_EDEVICE if a kernel flagged an error. */
+/* Block until the context stream is idle; PMSP_EDEVICE if a kernel flagged an error
+ * since the last report (the flag is then cleared, so it is reported once). */
 int pmsp_sync(pmsp_ctx* ctx);
 /* Fill *p with the defaults: d 0.3..10 m, 11x11 window at stride 2, 8
  * iterations, best_k 3, sigma_color 0.2, sigma_space 3 px, 6 refinement

@@ -412,7 +412,12 @@ int pmsp_sync(pmsp_ctx* c) {
     unsigned flag = 0;
     e = cudaMemcpy(&flag, c->d_err, sizeof flag, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "error flag read");
-    if (flag) return ctx_fail(c, PMSP_EDEVICE, "kernel error flag 0x%x", flag);
+    if (flag) {
+        // report once: the flag is cleared so later calls on the context start clean
+        e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+        if (e != cudaSuccess) return cuda_fail(c, e, "error flag reset");
+        return ctx_fail(c, PMSP_EDEVICE, "kernel error flag 0x%x", flag);
+    }
     return PMSP_OK;
 }
 
