@@ -41,9 +41,9 @@ OPS_PER_VIEW_SAMPLE = 55
 FP32_LANES_PER_SM = 128
 # DRAM bytes of one 6-view half-sweep launch at 1920x960 (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the current kernel build:
-# 49,830,656 read + 1,482,240 written). Set to None whenever the kernel changes
+# 49,830,656 read + 1,417,728 written). Set to None whenever the kernel changes
 # until it is captured again.
-SWEEP_DRAM_BYTES = 49_830_656 + 1_482_240
+SWEEP_DRAM_BYTES = 49_830_656 + 1_417_728
 
 
 def _dist():
@@ -241,7 +241,7 @@ def run_gpu(args):
         achieved = vs_per_sweep / (sweep_ms / 1e3)
         res["roofline"] = dict(bound="alu", achieved=achieved, peak=peak, unit="view-samples/s",
                                frac=achieved / peak, traffic=SWEEP_DRAM_BYTES, traffic_unit="bytes per launch",
-                               kernel="pixel_kernel<6, SWEEP> (one half-sweep)",
+                               kernel="pixel_kernel<6, SWEEP, 11x11/2 window> (one half-sweep)",
                                ms_per_launch=sweep_ms,
                                peak_basis=f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {peak_mhz:.0f} MHz / "
                                           f"{OPS_PER_VIEW_SAMPLE} ops per view-sample")
