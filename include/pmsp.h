@@ -12,7 +12,9 @@
  * consistency filter over neighbouring depth maps (Sec. III).
  *
  * Conventions (all calls):
- *  - Panorama W x H, row-major, W even. Pixel (u, v) looks along longitude
+ *  - Panorama W x H, row-major, W and H even for every image the
+ *    densification reads (references, sources, ring frames; PMSP_EINVAL
+ *    otherwise). Pixel (u, v) looks along longitude
  *    2*pi*(u+0.5)/W - pi and latitude pi/2 - pi*(v+0.5)/H; camera frame x right,
  *    y down, z forward.
  *  - Poses are world->camera, X_c = R X_w + t, R row-major, in double.

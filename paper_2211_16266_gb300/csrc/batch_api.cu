@@ -115,11 +115,11 @@ void batch_shutdown(pmsp_ctx* c) {
 static int check_item(pmsp_ctx* c, const pmsp_batch_item& it) {
     int rc = check_params(c, &it.params, it.n_src);
     if (rc) return rc;
-    if ((rc = check_image(c, &it.ref, "batch reference"))) return rc;
+    if ((rc = check_panorama(c, &it.ref, "batch reference"))) return rc;
     if (it.ref.w & 1) return ctx_fail(c, PMSP_EINVAL, "batch reference width %d must be even", it.ref.w);
     if (!it.srcs || !it.src_poses) return ctx_fail(c, PMSP_EINVAL, "batch item without sources");
     for (int s = 0; s < it.n_src; ++s)
-        if ((rc = check_image(c, &it.srcs[s], "batch source"))) return rc;
+        if ((rc = check_panorama(c, &it.srcs[s], "batch source"))) return rc;
     return check_maps(c, &it.out, it.ref.w, it.ref.h, true, true, "batch output");
 }
 

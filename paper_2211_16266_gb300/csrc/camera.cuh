@@ -91,10 +91,22 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // on the special-function unit. A direction exactly on the source's vertical
 // axis (X = Z = 0 in FP32) gives NaN coordinates; the view's NCC then clamps
 // to -1 and the view costs 2, as for an invalid sample (no fault: texture
-// fetches accept any coordinate). nsv = -sv. The paired cost path performs
+// fetches accept any coordinate).
+//
+// The pixel coordinates come out split so that their fractions are rounded
+// at the scale of a quarter panorama, not of a whole one, and so that the
+// whole columns and rows become constant texture offsets (W and H even). With
+// al = 2 atan(ql) (|al| <= pi/2): on the front half (front = Z >= 0)
+// u_c = su al + W/2 - 0.5 and qu = su al + 0.5 = u_c - (W/2 - 1); on the back
+// half u_c = -su al - 0.5 modulo W and qu = -su al + 0.5 = u_c + 1;
+// v_c = nsv (-lat) + H/2 - 0.5 and qv = nsv (-lat) + 0.5 = v_c - (H/2 - 1).
+// |qu| <= W/4 + 0.5, |qv| <= H/2 + 0.5. The gather footprint centre, the left
+// edge of texel floor(u_c) + 1, is then floor(qu) / W + 0.5 (front) or
+// floor(qu) / W (back), and floor(qv) / H + 0.5 in v: see
+// sample_bilinear_half. nsv = -sv = H / pi. The paired cost path performs
 // exactly these operations per lane after its rigid transform.
-__device__ __forceinline__ void project_dir_half(float X, float Y, float Z, float su, float ou, float nsv,
-                                                 float ov, float& uc, float& vc) {
+__device__ __forceinline__ void project_dir_half(float X, float Y, float Z, float su, float nsv, float& qu,
+                                                 float& qv, bool& front) {
     const float q = fmaf(X, X, Z * Z);
     const float rho = sqrt_approx(q);
     const float ql = X * rcp_approx(rho + fabsf(Z));
@@ -102,9 +114,9 @@ __device__ __forceinline__ void project_dir_half(float X, float Y, float Z, floa
     const float r3 = sqrt_approx(r2);
     const float qt = Y * rcp_approx(r3 + rho);
     const float al = ql * atan2x_poly(ql * ql), nlat = qt * atan2x_poly(qt * qt);
-    const float lon = Z >= 0.f ? al : copysignf(3.14159265358979324f, X) - al;
-    uc = fmaf(lon, su, ou);
-    vc = fmaf(nlat, nsv, ov);
+    front = Z >= 0.f;
+    qu = fmaf(al, front ? su : -su, 0.5f);
+    qv = fmaf(nlat, nsv, 0.5f);
 }
 
 // floor(x) for |x| < 2^22 with two FP32 adds: adding 1.5 * 2^23 rounded
@@ -126,6 +138,18 @@ __device__ __forceinline__ float sample_bilinear(cudaTextureObject_t tex, float 
     const float fi = floor_small(uc), fj = floor_small(vc);
     const float fx = uc - fi, fy = vc - fj;
     const float4 g = tex2Dgather<float4>(tex, fmaf(fi, inv_w, inv_w), fmaf(fj, inv_h, inv_h), 0);
+    const float top = fmaf(fx, g.z - g.w, g.w);
+    const float bot = fmaf(fx, g.y - g.x, g.x);
+    return fmaf(fy, bot - top, top);
+}
+
+// Bilinear fetch at split coordinates (see project_dir_half): the gather
+// addresses the 2 x 2 footprint at its centre in normalised coordinates.
+__device__ __forceinline__ float sample_bilinear_half(cudaTextureObject_t tex, float inv_w, float inv_h, float qu,
+                                                      float qv, bool front) {
+    const float fi = floor_small(qu), fj = floor_small(qv);
+    const float fx = qu - fi, fy = qv - fj;
+    const float4 g = tex2Dgather<float4>(tex, fmaf(fi, inv_w, front ? 0.5f : 0.0f), fmaf(fj, inv_h, 0.5f), 0);
     const float top = fmaf(fx, g.z - g.w, g.w);
     const float bot = fmaf(fx, g.y - g.x, g.x);
     return fmaf(fy, bot - top, top);

@@ -72,7 +72,7 @@ struct alignas(16) PixelParams {
     struct ViewPair {
         float2 R[9];
         float2 t[3];
-        float2 su, ou, nsv, ov;  // nsv = -sv: the paired projection computes -lat
+        float2 su, nsv;    // nsv = -sv: the paired projection computes -lat
         float2 inv_w, inv_h;
     } pairs[PMSP_MAX_SOURCES / 2];
 };

@@ -65,15 +65,16 @@ __device__ __forceinline__ float view_sample<LinearViews>(const SourceView& V, f
     const float Yx = fmaf(V.R[0], X, fmaf(V.R[1], Y, fmaf(V.R[2], Z, V.t[0])));
     const float Yy = fmaf(V.R[3], X, fmaf(V.R[4], Y, fmaf(V.R[5], Z, V.t[1])));
     const float Yz = fmaf(V.R[6], X, fmaf(V.R[7], Y, fmaf(V.R[8], Z, V.t[2])));
-    float uc, vc;
-    project_dir_half(Yx, Yy, Yz, V.su, V.ou, -V.sv, V.ov, uc, vc);
+    float qu, qv;
+    bool front;
+    project_dir_half(Yx, Yy, Yz, V.su, -V.sv, qu, qv, front);
     const LinearSrc& L = na_lin[s];
-    const float fi = floor_small(uc), fj = floor_small(vc);
-    const float fx = uc - fi, fy = vc - fj;
-    int i0 = (int)fi % L.w;
+    const float fi = floor_small(qu), fj = floor_small(qv);
+    const float fx = qu - fi, fy = qv - fj;
+    int i0 = ((int)fi + (front ? L.w / 2 - 1 : -1)) % L.w;  // see project_dir_half
     if (i0 < 0) i0 += L.w;
     const int i1 = i0 + 1 == L.w ? 0 : i0 + 1;
-    const int jj = (int)fj;
+    const int jj = (int)fj + L.h / 2 - 1;
     const int j0 = clamp_index(jj, L.h - 1), j1 = clamp_index(jj + 1, L.h - 1);
     const uint8_t* r0 = L.data + (int64_t)j0 * L.pitch;
     const uint8_t* r1 = L.data + (int64_t)j1 * L.pitch;
@@ -193,7 +194,7 @@ extern "C" int pmsp_densify_batch_noalloc(pmsp_ctx* c, const pmsp_batch_item* it
         const pmsp_batch_item& it = items[i];
         int rc = check_params(c, &it.params, it.n_src);
         if (rc) return rc;
-        if ((rc = check_image(c, &it.ref, "no-allocation reference"))) return rc;
+        if ((rc = check_panorama(c, &it.ref, "no-allocation reference"))) return rc;
         if ((rc = check_maps(c, &it.out, it.ref.w, it.ref.h, true, true, "no-allocation output"))) return rc;
         if (it.ref.w & 1) return ctx_fail(c, PMSP_EINVAL, "reference width %d must be even", it.ref.w);
         if (!it.srcs || !it.src_poses) return ctx_fail(c, PMSP_EINVAL, "item %d without sources", i);
@@ -205,7 +206,7 @@ extern "C" int pmsp_densify_batch_noalloc(pmsp_ctx* c, const pmsp_batch_item* it
         cudaTextureObject_t none[PMSP_MAX_SOURCES] = {};
         for (int s = 0; s < it.n_src; ++s) {
             const pmsp_image& im = it.srcs[s];
-            if ((rc = check_image(c, &im, "no-allocation source"))) return rc;
+            if ((rc = check_panorama(c, &im, "no-allocation source"))) return rc;
             if (im.memory != PMSP_DEVICE)
                 return ctx_fail(c, PMSP_EINVAL, "item %d: the no-allocation path takes device memory only", i);
             LinearSrc& L = lin[i * PMSP_MAX_SOURCES + s];

@@ -237,9 +237,10 @@ __device__ __forceinline__ float view_sample(const SourceView& V, float X, float
     const float Yx = fmaf(L.r(0), X, fmaf(L.r(1), Y, fmaf(L.r(2), Z, L.t(0))));
     const float Yy = fmaf(L.r(3), X, fmaf(L.r(4), Y, fmaf(L.r(5), Z, L.t(1))));
     const float Yz = fmaf(L.r(6), X, fmaf(L.r(7), Y, fmaf(L.r(8), Z, L.t(2))));
-    float uc, vc;
-    project_dir_half(Yx, Yy, Yz, L.su(), L.ou(), -L.sv(), L.ov(), uc, vc);
-    return sample_bilinear(L.tex(), L.inv_w(), L.inv_h(), uc, vc);
+    float qu, qv;
+    bool front;
+    project_dir_half(Yx, Yy, Yz, L.su(), -L.sv(), qu, qv, front);
+    return sample_bilinear_half(L.tex(), L.inv_w(), L.inv_h(), qu, qv, front);
 }
 
 // Cost of plane (range d along rp, unit normal n) at the pixel. Returns 2 for
@@ -364,12 +365,13 @@ __device__ __forceinline__ float2 pair_sample(const PixelParams::ViewPair& VP, c
     float2 pl, pt;
     atan2x_poly2_dual(mul2(ql, ql), mul2(qt, qt), pl, pt);
     const float2 al = mul2(ql, pl), nlat = mul2(qt, pt);
-    const float2 lon = make_float2(Yz.x >= 0.f ? al.x : copysignf(3.14159265358979324f, Yx.x) - al.x,
-                                   Yz.y >= 0.f ? al.y : copysignf(3.14159265358979324f, Yx.y) - al.y);
-    const float2 uc = fma2(lon, VP.su, VP.ou), vc = fma2(nlat, VP.nsv, VP.ov);
-    const float2 fi = floor_small2(uc), fj = floor_small2(vc);
-    const float2 fx = add2(uc, make_float2(-fi.x, -fi.y)), fy = add2(vc, make_float2(-fj.x, -fj.y));
-    const float2 xn = fma2(fi, VP.inv_w, VP.inv_w), yn = fma2(fj, VP.inv_h, VP.inv_h);
+    const bool f0 = Yz.x >= 0.f, f1 = Yz.y >= 0.f;
+    const float2 qu = fma2(al, make_float2(f0 ? VP.su.x : -VP.su.x, f1 ? VP.su.y : -VP.su.y), pair(0.5f));
+    const float2 qv = fma2(nlat, VP.nsv, pair(0.5f));
+    const float2 fi = floor_small2(qu), fj = floor_small2(qv);
+    const float2 fx = add2(qu, make_float2(-fi.x, -fi.y)), fy = add2(qv, make_float2(-fj.x, -fj.y));
+    const float2 xn = fma2(fi, VP.inv_w, make_float2(f0 ? 0.5f : 0.0f, f1 ? 0.5f : 0.0f));
+    const float2 yn = fma2(fj, VP.inv_h, pair(0.5f));
     const float4 g0 = tex2Dgather<float4>(V0.tex, xn.x, yn.x, 0);
     const float4 g1 = tex2Dgather<float4>(V1.tex, xn.y, yn.y, 0);
     const float top0 = fmaf(fx.x, g0.z - g0.w, g0.w), bot0 = fmaf(fx.x, g0.y - g0.x, g0.x);

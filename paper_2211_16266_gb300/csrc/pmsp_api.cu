@@ -75,6 +75,14 @@ int check_image(pmsp_ctx* c, const pmsp_image* im, const char* what) {
     return PMSP_OK;
 }
 
+int check_panorama(pmsp_ctx* c, const pmsp_image* im, const char* what) {
+    const int rc = check_image(c, im, what);
+    if (rc) return rc;
+    if ((im->w | im->h) & 1)  // the projection folds W/2 and H/2 into constant offsets (project_dir_half)
+        return ctx_fail(c, PMSP_EINVAL, "%s: size %dx%d must be even in both directions", what, im->w, im->h);
+    return PMSP_OK;
+}
+
 // Reference->target pose in FP64: R = R_t R_r^T, t = t_t - R t_r.
 void compose_rel(const pmsp_pose& r, const pmsp_pose& s, double R[9], double t[3]) {
     for (int i = 0; i < 3; ++i)
@@ -194,11 +202,11 @@ int prepare_problem(pmsp_ctx* c, const pmsp_image* ref, const pmsp_pose* ref_pos
                     const pmsp_pose* src_poses, int n_src, const pmsp_params* p, PixelParams& P) {
     int rc = check_params(c, p, n_src);
     if (rc) return rc;
-    if ((rc = check_image(c, ref, "reference"))) return rc;
+    if ((rc = check_panorama(c, ref, "reference"))) return rc;
     if (ref->w & 1) return ctx_fail(c, PMSP_EINVAL, "reference width %d must be even", ref->w);
     if (!ref_pose || !srcs || !src_poses) return ctx_fail(c, PMSP_EINVAL, "NULL pose or source array");
     for (int s = 0; s < n_src; ++s)
-        if ((rc = check_image(c, &srcs[s], "source"))) return rc;
+        if ((rc = check_panorama(c, &srcs[s], "source"))) return rc;
 
     if ((int)c->src_tex.size() < n_src) c->src_tex.resize(n_src);
     cudaTextureObject_t tex[PMSP_MAX_SOURCES];
@@ -250,9 +258,7 @@ void fill_problem(PixelParams& P, const pmsp_image* ref, const void* ref_dev, in
         for (int k = 0; k < 9; ++k) VP.R[k] = make_float2(A.R[k], B.R[k]);
         for (int k = 0; k < 3; ++k) VP.t[k] = make_float2(A.t[k], B.t[k]);
         VP.su = make_float2(A.su, B.su);
-        VP.ou = make_float2(A.ou, B.ou);
         VP.nsv = make_float2(-A.sv, -B.sv);
-        VP.ov = make_float2(A.ov, B.ov);
         VP.inv_w = make_float2(A.inv_w, B.inv_w);
         VP.inv_h = make_float2(A.inv_h, B.inv_h);
     }

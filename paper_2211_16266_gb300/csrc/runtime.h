@@ -32,6 +32,8 @@ int cuda_fail(pmsp_ctx* c, cudaError_t e, const char* what);
 void runtime_shutdown(pmsp_ctx* c);
 size_t format_bytes(int fmt);
 int check_image(pmsp_ctx* c, const pmsp_image* im, const char* what);
+// check_image plus even width and height: every image the densification reads.
+int check_panorama(pmsp_ctx* c, const pmsp_image* im, const char* what);
 int check_params(pmsp_ctx* c, const pmsp_params* p, int n_src);
 int check_maps(pmsp_ctx* c, const pmsp_maps* m, int W, int H, bool need_normal, bool need_cost, const char* what);
 int ensure_buffer(pmsp_ctx* c, DevBuffer& b, size_t bytes);

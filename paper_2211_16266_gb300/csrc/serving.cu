@@ -401,7 +401,7 @@ extern "C" {
 int pmsp_ring_push(pmsp_ctx* c, int64_t id, const pmsp_image* img, const pmsp_pose* pose) {
     if (!c) return PMSP_EINVAL;
     cudaSetDevice(c->device);
-    int rc = check_image(c, img, "ring frame");
+    int rc = check_panorama(c, img, "ring frame");
     if (rc) return rc;
     if (!pose) return ctx_fail(c, PMSP_EINVAL, "NULL pose");
     Serving& s = serving(c);

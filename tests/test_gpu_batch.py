@@ -41,7 +41,7 @@ def _problems():
     out.append(p0)
     p1 = scenes.config1(W=384, H=192)
     out.append(p1)
-    p2 = scenes.trajectory_problem(250, 131, 3, seed_scene=1010)
+    p2 = scenes.trajectory_problem(250, 130, 3, seed_scene=1010)
     p2.params = dict(d_min=0.3, d_max=10.0, patch_w=9, patch_stride=3, iterations=3, best_k=2, sigma_color=0.15,
                      sigma_space=4.0, n_refine=6, neighbor_table=1, seed=5, keyframe_id=77)
     out.append(p2)
