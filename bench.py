@@ -348,7 +348,8 @@ BATCH_CLASSES = ((960, 480, 12), (1920, 960, 14), (3840, 1920, 6))
 
 class ClassFrames:
     """Frames of one resolution class rendered along one trajectory (ss=1). uint8 images are
-    quantised DN; fp16 / fp32 images hold the unquantised render / 255."""
+    quantised DN; fp32 images hold the unquantised render / 255, fp16 images the same
+    minus 0.5."""
 
     def __init__(self, W, H, n, seed, fmt, with_range=False):
         import scenes
@@ -361,8 +362,12 @@ class ClassFrames:
             img, rg = scene.render(R, t, W, H, ss=1, with_range=with_range)
             if fmt == "u8":
                 im = scenes.quantise_u8(img)
+            elif fmt == "f16":
+                # centred on 0: fp16 rounding is finer near 0, and the cost depends on
+                # intensity differences and correlations only
+                im = (img / 255.0 - 0.5).astype(np.float16)
             else:
-                im = (img / 255.0).astype(np.float16 if fmt == "f16" else np.float32)
+                im = (img / 255.0).astype(np.float32)
             self.frames.append((im, (R, t)))
             self.ranges.append(rg)
 

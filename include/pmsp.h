@@ -21,8 +21,10 @@
  *  - "Depth" is the range along the pixel ray, metres. Normals are unit vectors
  *    in the reference camera frame, stored as three planes nx, ny, nz of W*H
  *    floats each (normal[0..N), normal[N..2N), normal[2N..3N)).
- *  - uint8 images are intensities DN/255; fp16/fp32 images are taken as given
- *    and are expected to lie in [0, 1].
+ *  - uint8 images are intensities DN/255; fp16/fp32 images are taken as given,
+ *    on the scale of [0, 1] (sigma_color refers to it). Any offset is allowed:
+ *    the cost depends on intensity differences and normalised correlations
+ *    only, and fp16 images centred on 0 (DN/255 - 0.5) round half as coarsely.
  *  - Ownership: the caller owns every buffer passed in and out; the library
  *    never frees or retains caller memory beyond a call. The context owns its
  *    internal buffers (texture arrays, staging, error flag) and frees them in
