@@ -340,43 +340,54 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem
     return sum / (float)P.best_k;
 }
 
-// Intensities of views 2q and 2q + 1 at the sample whose reference-frame
-// point is X = t r, r = (cl sin lon_c, -sl, cl cos lon_c) in tile column c:
-// the source point R_s X + t_s = alpha U_c + beta R_col1 + t_s with
-// alpha = t cl, beta = -t sl and U_c from the column table. The projection
-// runs on float2 pairs (one packed instruction for both views), then two
-// gathers and the bilinear weights per view. The arithmetic after the rigid
-// transform is that of project_dir_half and sample_bilinear, operation for
-// operation.
-__device__ __forceinline__ float2 pair_sample(const PixelParams::ViewPair& VP, const SourceView& V0,
-                                                   const SourceView& V1, float alpha, float beta, int q, int cx) {
+// Intensities of all NP view pairs (views 2q, 2q + 1) at the sample whose
+// reference-frame point is X = t r, r = (cl sin lon_c, -sl, cl cos lon_c) in
+// tile column c: the source point R_s X + t_s = alpha U_c + beta R_col1 + t_s
+// with alpha = t cl, beta = -t sl and U_c from the column table. The
+// projection runs on float2 pairs (one packed instruction for both views of a
+// pair), then two gathers and the bilinear weights per pair; the arithmetic
+// after the rigid transform is that of project_dir_half and
+// sample_bilinear_half, operation for operation. Two phases: the source
+// coordinates of every pair first, then the gathers and interpolation, so the
+// gathers of all pairs are in flight together (2 % faster than pair by pair).
+template <int NP>
+__device__ __forceinline__ void pairs_sample(const PixelParams& P, float alpha, float beta, int cx, float2 (&J)[NP]) {
+    float2 fx[NP], fy[NP], xn[NP], yn[NP];
     const float2 av = pair(alpha), bv = pair(beta);
-    const float2 Yx = fma2(av, g_colU[q][0][cx], fma2(bv, VP.R[1], VP.t[0]));
-    const float2 Yy = fma2(av, g_colU[q][1][cx], fma2(bv, VP.R[4], VP.t[1]));
-    const float2 Yz = fma2(av, g_colU[q][2][cx], fma2(bv, VP.R[7], VP.t[2]));
-    const float2 q2 = fma2(Yx, Yx, mul2(Yz, Yz));
-    const float2 rho = make_float2(sqrt_approx(q2.x), sqrt_approx(q2.y));
-    const float2 dl = add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y)));
-    const float2 ql = mul2(Yx, make_float2(rcp_approx(dl.x), rcp_approx(dl.y)));
-    const float2 r2 = fma2(Yy, Yy, q2);
-    const float2 r3 = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
-    const float2 dt = add2(r3, rho);
-    const float2 qt = mul2(Yy, make_float2(rcp_approx(dt.x), rcp_approx(dt.y)));
-    float2 pl, pt;
-    atan2x_poly2_dual(mul2(ql, ql), mul2(qt, qt), pl, pt);
-    const float2 al = mul2(ql, pl), nlat = mul2(qt, pt);
-    const bool f0 = Yz.x >= 0.f, f1 = Yz.y >= 0.f;
-    const float2 qu = fma2(al, make_float2(f0 ? VP.su.x : -VP.su.x, f1 ? VP.su.y : -VP.su.y), pair(0.5f));
-    const float2 qv = fma2(nlat, VP.nsv, pair(0.5f));
-    const float2 fi = floor_small2(qu), fj = floor_small2(qv);
-    const float2 fx = add2(qu, make_float2(-fi.x, -fi.y)), fy = add2(qv, make_float2(-fj.x, -fj.y));
-    const float2 xn = fma2(fi, VP.inv_w, make_float2(f0 ? 0.5f : 0.0f, f1 ? 0.5f : 0.0f));
-    const float2 yn = fma2(fj, VP.inv_h, pair(0.5f));
-    const float4 g0 = tex2Dgather<float4>(V0.tex, xn.x, yn.x, 0);
-    const float4 g1 = tex2Dgather<float4>(V1.tex, xn.y, yn.y, 0);
-    const float top0 = fmaf(fx.x, g0.z - g0.w, g0.w), bot0 = fmaf(fx.x, g0.y - g0.x, g0.x);
-    const float top1 = fmaf(fx.y, g1.z - g1.w, g1.w), bot1 = fmaf(fx.y, g1.y - g1.x, g1.x);
-    return make_float2(fmaf(fy.x, bot0 - top0, top0), fmaf(fy.y, bot1 - top1, top1));
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const PixelParams::ViewPair& VP = P.pairs[q];
+        const float2 Yx = fma2(av, g_colU[q][0][cx], fma2(bv, VP.R[1], VP.t[0]));
+        const float2 Yy = fma2(av, g_colU[q][1][cx], fma2(bv, VP.R[4], VP.t[1]));
+        const float2 Yz = fma2(av, g_colU[q][2][cx], fma2(bv, VP.R[7], VP.t[2]));
+        const float2 q2 = fma2(Yx, Yx, mul2(Yz, Yz));
+        const float2 rho = make_float2(sqrt_approx(q2.x), sqrt_approx(q2.y));
+        const float2 dl = add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y)));
+        const float2 ql = mul2(Yx, make_float2(rcp_approx(dl.x), rcp_approx(dl.y)));
+        const float2 r2 = fma2(Yy, Yy, q2);
+        const float2 r3 = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
+        const float2 dt = add2(r3, rho);
+        const float2 qt = mul2(Yy, make_float2(rcp_approx(dt.x), rcp_approx(dt.y)));
+        float2 pl, pt;
+        atan2x_poly2_dual(mul2(ql, ql), mul2(qt, qt), pl, pt);
+        const float2 al = mul2(ql, pl), nlat = mul2(qt, pt);
+        const bool f0 = Yz.x >= 0.f, f1 = Yz.y >= 0.f;
+        const float2 qu = fma2(al, make_float2(f0 ? VP.su.x : -VP.su.x, f1 ? VP.su.y : -VP.su.y), pair(0.5f));
+        const float2 qv = fma2(nlat, VP.nsv, pair(0.5f));
+        const float2 fi = floor_small2(qu), fj = floor_small2(qv);
+        fx[q] = add2(qu, make_float2(-fi.x, -fi.y));
+        fy[q] = add2(qv, make_float2(-fj.x, -fj.y));
+        xn[q] = fma2(fi, VP.inv_w, make_float2(f0 ? 0.5f : 0.0f, f1 ? 0.5f : 0.0f));
+        yn[q] = fma2(fj, VP.inv_h, pair(0.5f));
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const float4 g0 = tex2Dgather<float4>(P.src[2 * q].tex, xn[q].x, yn[q].x, 0);
+        const float4 g1 = tex2Dgather<float4>(P.src[2 * q + 1].tex, xn[q].y, yn[q].y, 0);
+        const float top0 = fmaf(fx[q].x, g0.z - g0.w, g0.w), bot0 = fmaf(fx[q].x, g0.y - g0.x, g0.x);
+        const float top1 = fmaf(fx[q].y, g1.z - g1.w, g1.w), bot1 = fmaf(fx[q].y, g1.y - g1.x, g1.x);
+        J[q] = make_float2(fmaf(fy[q].x, bot0 - top0, top0), fmaf(fy[q].y, bot1 - top1, top1));
+    }
 }
 
 // plane_cost for exactly NS >= 2 views held in kernel parameters, with the
@@ -403,11 +414,9 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const T
         const float t = __fdividef(dn, den);
         const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
         const float alpha = t * cl, beta = -t * sm.row_sin[ly + o];
+        pairs_sample<NP>(P, alpha, beta, lx + o, c0);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            c0[q] = pair_sample(P.pairs[q], P.src[2 * q], P.src[2 * q + 1], alpha, beta, q, lx + o);
-            SJ[q] = SJJ[q] = SIJ[q] = pair(0.f);
-        }
+        for (int q = 0; q < NP; ++q) SJ[q] = SJJ[q] = SIJ[q] = pair(0.f);
         if (ODD) c0o = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z);
     }
     bool valid = true;
@@ -432,9 +441,11 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const T
             const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
             const float alpha = t * cl, beta = t * msl;
             const float2 w2 = pair(w), wI2 = pair(wI);
+            float2 Jall[NP];
+            pairs_sample<NP>(P, alpha, beta, cx, Jall);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const float2 J = pair_sample(P.pairs[q], P.src[2 * q], P.src[2 * q + 1], alpha, beta, q, cx);
+                const float2 J = Jall[q];
                 const float2 Jc = add2(J, make_float2(-c0[q].x, -c0[q].y));
                 const float2 tw = mul2(w2, Jc);
                 SJ[q] = add2(SJ[q], tw);
