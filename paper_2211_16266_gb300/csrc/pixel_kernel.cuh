@@ -10,15 +10,18 @@
 // reprojection through the plane into every source, averaged over the best k
 // views (the cost of the PatchMatch works the paper cites).
 //
-// Design: one thread per active pixel of a 32x8 tile (one colour per launch).
-// The reference tile with its halo, the per-row / per-column bearing terms
-// and the spatial weights are staged in shared memory; the sample loop runs
-// over the patch with all views innermost, so the plane intersection and the
-// bilateral weight of a sample are shared by every view. Per view four FP32
-// sums are kept: the source intensity is centred on its value at the first
-// (centre-most) sample, which keeps the variance term free of cancellation.
-// The 8 neighbour candidates and the refinement candidates run through one
-// loop with a single inlined copy of the cost.
+// Design: one thread per active pixel of a 32x8 tile (one colour per launch),
+// blocks walking the image in strips of tile rows. The reference tile with
+// its halo, the per-row / per-column bearing terms, the spatial weights and
+// (for exactly known view counts) each view pair's rotated column directions
+// are staged in shared memory; the sample loop runs over the patch with all
+// views innermost, so the plane intersection and the bilateral weight of a
+// sample are shared by every view. Views are processed in pairs with packed
+// FP32 instructions, the projection in half-angle form (see camera.cuh). Per
+// view four FP32 sums are kept: the source intensity is centred on its value
+// at the first (centre-most) sample, which keeps the variance term free of
+// cancellation. The 8 neighbour candidates and the refinement candidates run
+// through one loop with a single inlined copy of the cost.
 #pragma once
 
 #include <cuda_fp16.h>
