@@ -143,6 +143,14 @@ def problem_of(frames, k):
     return frames[k], srcs
 
 
+def keyframe_config(world_size: int) -> dict:
+    """The keyframe workload's description, the same for both arms."""
+    return dict(workload=WORKLOAD, image_storage="u8", width=W, height=H, sources=N_SRC, iterations=ITERS,
+                window="11x11/2", best_k=3, filter_neighbours=N_NEIGHBOURS,
+                l2="flushed (256 MiB write) between steps",
+                parallelism="replicas" if world_size > 1 else "single")
+
+
 def algorithmic_counts():
     evals = W * H * (1 + ITERS * (8 + 6))
     view_samples = evals * N_SRC * 36
@@ -225,10 +233,8 @@ def run_gpu(args):
     res = dict(
         metric=METRIC, value=replica_throughput(ws, args.steps, total_ms), unit="keyframes/s", n_gpus=ws,
         steps=args.steps, warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
-        scaling="weak", vs_baseline=None, dtype="u8 images, f32 math", data="synthetic",
-        config=dict(workload=WORKLOAD, width=W, height=H, sources=N_SRC, iterations=ITERS, window="11x11/2",
-                    best_k=3, filter_neighbours=N_NEIGHBOURS, l2="flushed (256 MiB write) between steps",
-                    parallelism="replicas" if ws > 1 else "single"),
+        scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config=keyframe_config(ws),
         latency_ms=dict(p50=float(np.percentile(times, 50)), p99=float(np.percentile(times, 99))),
         hypothesis_evals_per_s=ws * evals * args.steps / (total_ms / 1e3),
         gpu_launches=args.steps * (2 + 2 * ITERS + 1),
@@ -339,7 +345,7 @@ def run_reference(args):
     print(json.dumps(dict(impl="reference", metric=METRIC, value=val, unit="keyframes/s", n_gpus=ws,
                           steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * sum(per) / args.steps,
                           higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-                          data="synthetic", config=dict(workload=WORKLOAD), cpu_baseline=cb,
+                          data="synthetic", config=keyframe_config(ws), cpu_baseline=cb,
                           e2e=dict(value=val, unit="keyframes/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))))
 
 
@@ -459,8 +465,8 @@ def run_batched(args):
         metric="keyframes/s, 32 mixed keyframes (12x960x480, 14x1920x960, 6x3840x1920), 4-10 views",
         value=n / (res["batched_f16"] / 1e3), unit="keyframes/s", n_gpus=1, steps=args.steps, warmup=1,
         ms_per_step=res["batched_f16"], higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="f16 images, f32 math", data="synthetic",
-        config=dict(workload="batched form: one batch of 32 keyframes, CUDA graph, autotuned",
+        dtype="f32", data="synthetic",
+        config=dict(workload="batched form: one batch of 32 keyframes, CUDA graph, autotuned", image_storage="f16",
                     tuning=res["tuning"], forms=forms))))
     ctx.close()
 
@@ -585,9 +591,10 @@ def run_serving(args):
         metric="p50/p99 latency and keyframes/s, Poisson 4/s + 12/s bursts, mixed sizes",
         value=out["served_f16"]["keyframes_per_s"], unit="keyframes/s", n_gpus=1, steps=n_req, warmup=0,
         ms_per_step=1e3 * out["served_f16"]["wall_s"] / n_req, higher_is_better=True, scaling="weak",
-        vs_baseline=None, dtype="f16 images, f32 math", data="synthetic",
+        vs_baseline=None, dtype="f32", data="synthetic",
         latency_ms=dict(p50=out["served_f16"]["p50_ms"], p99=out["served_f16"]["p99_ms"]),
         config=dict(workload=f"serving form: {n_req} requests over a 64-frame ring, continuous batching",
+                    image_storage="f16",
                     plain_fifo_u8=out["plain_u8"], plain_fifo_f32=out["plain_f32"]))))
 
 
@@ -671,8 +678,8 @@ def run_pipeline(args):
         metric="keyframes/s of the online pipeline (densify + consistency + median + fusion + completeness)",
         value=main_r["keyframes_per_s"], unit="keyframes/s", n_gpus=1, steps=len(keys), warmup=0,
         ms_per_step=1e3 / main_r["keyframes_per_s"], higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="u8 images, f32 math", data="synthetic",
-        config=dict(workload="online pipeline: 10 keyframes 1920x960 along a 16-frame walk, 6 views, 11x11/2, "
+        dtype="f32", data="synthetic",
+        config=dict(image_storage="u8", workload="online pipeline: 10 keyframes 1920x960 along a 16-frame walk, 6 views, 11x11/2, "
                              "best-3, filter vs 4 keyframes, median 5x5/5 %, 1 cm voxels, 720x360 completeness"),
         runs=out)))
 
