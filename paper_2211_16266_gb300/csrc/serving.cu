@@ -134,9 +134,10 @@ int dev_alloc(DevBuffer& b, size_t bytes, cudaStream_t st) {
     return PMSP_OK;
 }
 
-// Tiles of resident work admission aims for: about two waves of the sweep
-// kernel's resident blocks. More would only stretch every running request's
-// latency; a request that alone exceeds it still runs.
+// Tiles of resident work admission aims for: about two waves of six resident
+// 128-thread blocks per SM (the sweep kernels keep 4 to 7). More would only
+// stretch every running request's latency; a request that alone exceeds it
+// still runs.
 size_t tile_budget(const Serving& s) { return (size_t)s.sms * 6 * 2; }
 
 // Give back a request's frames and maps (stream-ordered free: no device-wide sync).
@@ -144,7 +145,9 @@ void release_request(Serving& s, Request* r) {
     for (int f : r->srcs) s.ring[f].pins--;
     for (int f : r->filters) s.ring[f].pins--;
     s.ring[r->ref].pins--;
-    if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, s.upload);
+    // freed in the order of the stream the request's work ran on, so a request
+    // whose launch chain failed part-way cannot have its maps reused under it
+    if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, r->lane >= 0 ? s.lanes[r->lane] : s.upload);
     if (r->done) cudaEventDestroy(r->done);
     if (r->maps.ptr) s.bytes_in_use -= r->bytes;
     delete r;

@@ -163,3 +163,16 @@ def test_completeness_matches_oracle(pm, walk):
             ch, _ = pm.pmsp_completeness(ctx, P.astype(np.float32), walk[k][0], 720, 360, hit=hh)
             assert ch == c and np.array_equal(hh.astype(bool), hit)
             print(f"keyframe {k}: completeness {c:.4f} (oracle {co:.4f}), {unclear} points near a pixel edge")
+
+
+def test_view_filter_and_completeness_errors(pm):
+    pts = np.zeros((4, 3), np.float32)
+    pose = (np.eye(3), np.zeros(3))
+    with pm.Context(0) as ctx:
+        for kw in (dict(min_deg=30.0, max_deg=10.0), dict(max_deg=181.0), dict(min_frac=1.5), dict(min_deg=-1.0)):
+            with pytest.raises(pm.PmspError) as e:
+                pm.pmsp_view_filter(ctx, pose, pose, pts, **kw)
+            assert e.value.code == pm.PMSP_EINVAL
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_completeness(ctx, pts, pose, 0, 10)
+        assert e.value.code == pm.PMSP_EINVAL
