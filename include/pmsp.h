@@ -9,7 +9,11 @@
  * (Sec. III-C, item 1), scored by a bilaterally weighted NCC of the reference
  * patch against its reprojection through the plane into every source
  * panorama, averaged over the best k views; and a multi-view geometric
- * consistency filter over neighbouring depth maps (Sec. III).
+ * consistency filter over neighbouring depth maps (Sec. III). Around that
+ * path: initialisation by plane-map warping (Sec. III-B), the median
+ * post-filter (Sec. III-C, item 2), the View Filter (Sec. III-A, Eq. 1),
+ * point-cloud fusion (Sec. III) and keyframe completeness (Sec. IV); batched
+ * and served forms of the densification.
  *
  * Conventions (all calls):
  *  - Panorama W x H, row-major, W and H even for every image the
@@ -35,8 +39,9 @@
  *  - Streams: work is enqueued on the context's stream. A call whose inputs
  *    and outputs are all device memory returns once the work is enqueued
  *    (asynchronous); a call touching host memory returns after the results
- *    are back on the host. pmsp_sync waits for the stream and reports any
- *    error the kernels flagged.
+ *    are back on the host, and so do the calls that return counts
+ *    (pmsp_view_filter, pmsp_fuse, pmsp_completeness). pmsp_sync waits for
+ *    the stream and reports any error the kernels flagged.
  *  - Threads: a context is used by one host thread at a time, except the
  *    serving calls (submit/poll/wait), which are internally locked.
  */
@@ -140,11 +145,11 @@ void pmsp_default_params(pmsp_params* p);
  * black half-sweeps of Sec. III-C propagation and refinement).
  *   ref, ref_pose        reference panorama and pose
  *   srcs, src_poses      n_src source panoramas (1 <= n_src <= PMSP_MAX_SOURCES),
- *                        any size each, and their poses
+ *                        any even size each, and their poses
  *   p                    parameters
  *   out                  w x h of the reference; depth, normal, cost all required.
- * Returns PMSP_EINVAL for odd w, best_k outside [1, n_src], a bad window, a bad
- * range, a NULL pointer or an unknown format.
+ * Returns PMSP_EINVAL for an odd width or height, best_k outside [1, n_src], a
+ * bad window, a bad range, a NULL pointer or an unknown format.
  */
 int pmsp_densify(pmsp_ctx* ctx, const pmsp_image* ref, const pmsp_pose* ref_pose,
                  const pmsp_image* srcs, const pmsp_pose* src_poses, int n_src,
