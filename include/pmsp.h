@@ -342,6 +342,9 @@ typedef struct {
     int32_t strategy;      /* 0: one persistent launch per phase over all keyframes' tiles;
                               1: every keyframe's own launch chain, chains run concurrently on
                                  parallel streams (parallel branches of the captured graph) */
+    int32_t tile;          /* strategy 1, half-sweeps with an 11x11/2 or 7x7/1 window: tile of
+                              reference pixels per 128-thread block, 0: 32x8, 1: 64x4, 2: 16x16
+                              (every shape computes the same numbers) */
 } pmsp_tuning;
 
 #define PMSP_BATCH_GRAPH 1u /* capture the batch in a CUDA graph and replay it when the identical

@@ -63,6 +63,7 @@ struct alignas(16) PixelParams {
     float ws;             // -log2(e) / (2 sigma_s^2), 0 when off
     unsigned long long seed, keyframe;
     int phase;            // batched serving: 0,1 initialisation colours, 2 + 2 t + c half-sweep (t, c)
+    int tile;             // tile shape of the single-keyframe half-sweep: 0 32x8, 1 64x4, 2 16x16
     int colour;
     int iter;
     unsigned* err;

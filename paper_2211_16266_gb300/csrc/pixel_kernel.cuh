@@ -52,19 +52,33 @@ constexpr int min_blocks_for(int ns) { return ns <= 4 ? 8 : ns <= 6 ? 7 : ns <= 
 // alone takes up to 246). Measured on 1920x960 half-sweeps.
 constexpr int pixel_min_blocks(int ns) { return ns <= 6 ? 7 : ns <= 8 ? 5 : 4; }
 
-struct TileSmem {
-    float ref[TILE_ROWS * TILE_PITCH];  // normalised intensities, halo included
-    float row_cos[TILE_ROWS], row_sin[TILE_ROWS];    // cos lat, sin lat
-    float col_sin[TILE_PITCH], col_cos[TILE_PITCH];  // sin lon, cos lon
-    float wsp[MAX_K];                                // spatial log2-weight of offset index k
+// Shared memory of one tile of TW x TH reference pixels (halo included);
+// every shape has (TW / 2) x TH = 128 threads, one per pixel of one colour.
+template <int TW, int TH>
+struct TileSmemT {
+    static constexpr int W = TW, H = TH;
+    static constexpr int PITCH = TW + 2 * MAX_HALO, ROWS = TH + 2 * MAX_HALO;
+    static constexpr int THREADS = (TW / 2) * TH;
+    static_assert(THREADS == BLOCK_THREADS, "every tile shape runs 128 threads");
+    float ref[ROWS * PITCH];             // normalised intensities, halo included
+    float row_cos[ROWS], row_sin[ROWS];  // cos lat, sin lat
+    float col_sin[PITCH], col_cos[PITCH];  // sin lon, cos lon
+    float wsp[MAX_K];                    // spatial log2-weight of offset index k
 };
+using TileSmem = TileSmemT<TILE_W, TILE_H>;  // the batched and no-alloc kernels' shape
+
+// Tile shapes of the single-keyframe half-sweep, chosen by PixelParams::tile.
+template <int TS> struct TileShape { using Smem = TileSmemT<32, 8>; };
+template <> struct TileShape<1> { using Smem = TileSmemT<64, 4>; };
+template <> struct TileShape<2> { using Smem = TileSmemT<16, 16>; };
+constexpr int MAX_TILE_PITCH = 64 + 2 * MAX_HALO;
 
 // Rotated column directions of the paired path: for view pair q and tile
 // column c, colU[q][k][c] = row k of R_s applied to (sin lon_c, 0, cos lon_c)
 // for both views of the pair. A sample direction r = (cl sin, -sl, cl cos)
 // then transforms as R r = cl U_c - sl R_col1.
 constexpr int MAX_COL_PAIRS = 5;
-__shared__ float2 g_colU[MAX_COL_PAIRS][3][TILE_PITCH];
+__shared__ float2 g_colU[MAX_COL_PAIRS][3][MAX_TILE_PITCH];
 
 // Sample window of the paired cost loop: WIN 0 reads the window from the
 // parameters; the fixed windows make the loop bounds and offsets constants
@@ -105,14 +119,15 @@ __device__ __forceinline__ float load_ref(const PixelParams& P, int x, int y) {
     return reinterpret_cast<const float*>(row)[x];
 }
 
-__device__ __forceinline__ void stage_tile(const PixelParams& P, TileSmem& sm, int bx, int by) {
+template <class SM>
+__device__ __forceinline__ void stage_tile(const PixelParams& P, SM& sm, int bx, int by) {
     const int R = P.radius;
-    const int rows = TILE_H + 2 * R, cols = TILE_W + 2 * R;
+    const int rows = SM::H + 2 * R, cols = SM::W + 2 * R;
     for (int i = threadIdx.x; i < rows * cols; i += BLOCK_THREADS) {
         const int ly = i / cols, lx = i - ly * cols;
         const int gy = clamp_index(by - R + ly, P.H - 1);
         const int gx = wrap_index(bx - R + lx, P.W);
-        sm.ref[ly * TILE_PITCH + lx] = load_ref(P, gx, gy);
+        sm.ref[ly * SM::PITCH + lx] = load_ref(P, gx, gy);
     }
     for (int i = threadIdx.x; i < rows; i += BLOCK_THREADS) {
         const int gy = clamp_index(by - R + i, P.H - 1);
@@ -135,20 +150,22 @@ __device__ __forceinline__ void stage_tile(const PixelParams& P, TileSmem& sm, i
 }
 
 // Bilateral weight of sample (a, b) with intensity Iq: 2^(wc dI^2 + ws |o|^2).
-__device__ __forceinline__ float bilateral(const PixelParams& P, const TileSmem& sm, int a, int b, float Iq,
+template <class SM>
+__device__ __forceinline__ float bilateral(const PixelParams& P, const SM& sm, int a, int b, float Iq,
                                            float Ip) {
     const float dI = Iq - Ip;
     return exp2_approx(fmaf(P.wc, dI * dI, sm.wsp[a] + sm.wsp[b]));
 }
 
 // Local (halo-inclusive) tile coordinates of the pixel: lx, ly.
-__device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const TileSmem& sm, int lx, int ly) {
+template <class SM>
+__device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const SM& sm, int lx, int ly) {
     RefStats st;
-    st.Ip = sm.ref[ly * TILE_PITCH + lx];
+    st.Ip = sm.ref[ly * SM::PITCH + lx];
     const int R = P.radius, stp = P.stride;
     float Sw = 0.f, SI = 0.f;
     for (int a = 0; a < P.K; ++a) {
-        const float* row = sm.ref + (ly + a * stp - R) * TILE_PITCH + lx - R;
+        const float* row = sm.ref + (ly + a * stp - R) * SM::PITCH + lx - R;
         for (int b = 0; b < P.K; ++b) {
             const float Iq = row[b * stp];
             const float w = bilateral(P, sm, a, b, Iq, st.Ip);
@@ -160,7 +177,7 @@ __device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const TileSm
     st.mu = SI / Sw;
     float SIc = 0.f, SIIc = 0.f;
     for (int a = 0; a < P.K; ++a) {
-        const float* row = sm.ref + (ly + a * stp - R) * TILE_PITCH + lx - R;
+        const float* row = sm.ref + (ly + a * stp - R) * SM::PITCH + lx - R;
         for (int b = 0; b < P.K; ++b) {
             const float Iq = row[b * stp];
             const float w = bilateral(P, sm, a, b, Iq, st.Ip);
@@ -249,8 +266,8 @@ __device__ __forceinline__ float view_sample(const SourceView& V, float X, float
 // Cost of plane (range d along rp, unit normal n) at the pixel. Returns 2 for
 // an invalid plane (a patch ray meets it from behind or grazing). NS views
 // are kept in registers; EXACT means S == NS (no per-view guard).
-template <int NS, bool EXACT, class VA>
-__device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem& sm, int lx, int ly,
+template <int NS, bool EXACT, class VA, class SM>
+__device__ __forceinline__ float plane_cost(const PixelParams& P, const SM& sm, int lx, int ly,
                                             const RefStats& st, float3 rp, float d, float3 n) {
     const float eps = 1e-8f * st.Sw * st.Sw;
     if (st.varI < eps) return 2.0f;
@@ -280,7 +297,7 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const TileSmem
     for (int a = 0; a < K && valid; ++a) {
         const int oy = a * stp - R;
         const float cl = sm.row_cos[ly + oy], msl = -sm.row_sin[ly + oy];
-        const float* ref_row = sm.ref + (ly + oy) * TILE_PITCH + lx - R;
+        const float* ref_row = sm.ref + (ly + oy) * SM::PITCH + lx - R;
         for (int b = 0; b < K; ++b) {
             if (a == ac && b == ac) continue;
             const float Iq = ref_row[b * stp];
@@ -395,8 +412,8 @@ __device__ __forceinline__ void pairs_sample(const PixelParams& P, float alpha, 
 
 // plane_cost for exactly NS >= 2 views held in kernel parameters, with the
 // views processed in pairs (packed FP32) and an odd last view on its own.
-template <int NS, int WIN>
-__device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const TileSmem& sm, int lx, int ly,
+template <int NS, int WIN, class SM>
+__device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const SM& sm, int lx, int ly,
                                                    const RefStats& st, float3 rp, float d, float3 n) {
     constexpr int NP = NS / 2;
     constexpr bool ODD = (NS & 1) != 0;
@@ -427,7 +444,7 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const T
     for (int a = 0; a < K; ++a) {
         const int oy = a * stp - R;
         const float cl = sm.row_cos[ly + oy], msl = -sm.row_sin[ly + oy];
-        const float* ref_row = sm.ref + (ly + oy) * TILE_PITCH + lx - R;
+        const float* ref_row = sm.ref + (ly + oy) * SM::PITCH + lx - R;
 #pragma unroll 1
         for (int b = 0; b < K; ++b) {
             if (a == ac && b == ac) continue;
@@ -499,13 +516,13 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const T
 
 // The cost used by the per-pixel kernels: the paired form where the views
 // are exactly known and sit in kernel parameters, the general one otherwise.
-template <int NS, bool EXACT, class VA, int WIN = 0>
-__device__ __forceinline__ float cost_of(const PixelParams& P, const TileSmem& sm, int lx, int ly,
+template <int NS, bool EXACT, class VA, int WIN = 0, class SM = TileSmem>
+__device__ __forceinline__ float cost_of(const PixelParams& P, const SM& sm, int lx, int ly,
                                          const RefStats& st, float3 rp, float d, float3 n) {
     if constexpr (EXACT && NS >= 2 && std::is_same<VA, ParamViews>::value)
-        return plane_cost_paired<NS, WIN>(P, sm, lx, ly, st, rp, d, n);
+        return plane_cost_paired<NS, WIN, SM>(P, sm, lx, ly, st, rp, d, n);
     else
-        return plane_cost<NS, EXACT, VA>(P, sm, lx, ly, st, rp, d, n);
+        return plane_cost<NS, EXACT, VA, SM>(P, sm, lx, ly, st, rp, d, n);
 }
 
 // Face the camera: n . r_p < 0 (|n . r_p| < 1e-3: replace by -r_p).
@@ -533,15 +550,15 @@ __device__ __forceinline__ void random_plane(const PixelParams& P, size_t i, flo
 // One tile of one problem: stage the reference tile, then every active
 // pixel of `colour` runs MODE. P may live in kernel parameters or in shared
 // memory (the batched kernel). Returns without a trailing barrier.
-template <int NS, bool EXACT, int MODE, class VA = ParamViews, int WIN = 0>
-__device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm, int bx, int by, int colour,
+template <int NS, bool EXACT, int MODE, class VA = ParamViews, int WIN = 0, class SM = TileSmem>
+__device__ __forceinline__ void process_tile(const PixelParams& P, SM& sm, int bx, int by, int colour,
                                              int iter) {
     stage_tile(P, sm, bx, by);
     __syncthreads();
     if constexpr (EXACT && NS >= 2 && std::is_same<VA, ParamViews>::value) {
         constexpr int NP = NS / 2;
         static_assert(NP <= MAX_COL_PAIRS, "column table too small");
-        const int cols = TILE_W + 2 * P.radius;
+        const int cols = SM::W + 2 * P.radius;
         for (int i = threadIdx.x; i < cols * NP; i += BLOCK_THREADS) {
             const int q = i / cols, c = i - q * cols;
             const PixelParams::ViewPair& VP = P.pairs[q];
@@ -553,7 +570,7 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm,
         __syncthreads();
     }
 
-    const int tx = threadIdx.x % (TILE_W / 2), ty = threadIdx.x / (TILE_W / 2);
+    const int tx = threadIdx.x % (SM::W / 2), ty = threadIdx.x / (SM::W / 2);
     const int y = by + ty;
     const int x = bx + 2 * tx + ((y + colour) & 1);
     if (x >= P.W || y >= P.H) return;
@@ -566,7 +583,7 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm,
 
     if (MODE == MODE_COST) {
         const float3 n = make_float3(P.nx[i], P.ny[i], P.nz[i]);
-        P.cost[i] = cost_of<NS, EXACT, VA, WIN>(P, sm, lx, ly, st, rp, P.depth[i], n);
+        P.cost[i] = cost_of<NS, EXACT, VA, WIN, SM>(P, sm, lx, ly, st, rp, P.depth[i], n);
         return;
     }
     if (MODE == MODE_INIT) {
@@ -577,7 +594,7 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm,
         P.nx[i] = n.x;
         P.ny[i] = n.y;
         P.nz[i] = n.z;
-        P.cost[i] = cost_of<NS, EXACT, VA, WIN>(P, sm, lx, ly, st, rp, d, n);
+        P.cost[i] = cost_of<NS, EXACT, VA, WIN, SM>(P, sm, lx, ly, st, rp, d, n);
         return;
     }
 
@@ -618,7 +635,7 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, TileSmem& sm,
             nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
         }
         if (ok) {
-            const float c = cost_of<NS, EXACT, VA, WIN>(P, sm, lx, ly, st, rp, dc, nc);
+            const float c = cost_of<NS, EXACT, VA, WIN, SM>(P, sm, lx, ly, st, rp, dc, nc);
             if (c < bc) {
                 bc = c;
                 bd = dc;
@@ -651,12 +668,30 @@ __device__ __forceinline__ void tile_of_block(int gx, int gy, int L, int& tx, in
     }
 }
 
-template <int NS, bool EXACT, int MODE, int WIN = 0>
+template <int NS, bool EXACT, int MODE, int WIN = 0, int TS = 0>
 __global__ void __launch_bounds__(BLOCK_THREADS, pixel_min_blocks(NS)) pixel_kernel(const __grid_constant__ PixelParams P) {
-    __shared__ TileSmem sm;
+    using SM = typename TileShape<TS>::Smem;
+    __shared__ SM sm;
     int tx, ty;
     tile_of_block(gridDim.x, gridDim.y, blockIdx.y * gridDim.x + blockIdx.x, tx, ty);
-    process_tile<NS, EXACT, MODE, ParamViews, WIN>(P, sm, tx * TILE_W, ty * TILE_H, P.colour, P.iter);
+    process_tile<NS, EXACT, MODE, ParamViews, WIN, SM>(P, sm, tx * SM::W, ty * SM::H, P.colour, P.iter);
+}
+
+// Grid of a tile shape over a W x H panorama.
+template <int TS>
+inline dim3 tile_grid(const PixelParams& p) {
+    using SM = typename TileShape<TS>::Smem;
+    return dim3((p.W + SM::W - 1) / SM::W, (p.H + SM::H - 1) / SM::H);
+}
+
+// A fixed-window sweep in the problem's tile shape.
+template <int NS, bool EXACT, int WIN>
+inline void launch_sweep_window(const PixelParams& p, cudaStream_t stream) {
+    switch (p.tile) {
+        case 1: pixel_kernel<NS, EXACT, MODE_SWEEP, WIN, 1><<<tile_grid<1>(p), BLOCK_THREADS, 0, stream>>>(p); break;
+        case 2: pixel_kernel<NS, EXACT, MODE_SWEEP, WIN, 2><<<tile_grid<2>(p), BLOCK_THREADS, 0, stream>>>(p); break;
+        default: pixel_kernel<NS, EXACT, MODE_SWEEP, WIN, 0><<<tile_grid<0>(p), BLOCK_THREADS, 0, stream>>>(p); break;
+    }
 }
 
 // The window class of a problem: a fixed-window sweep instance where one exists.
@@ -674,15 +709,15 @@ cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t 
         case MODE_INIT: pixel_kernel<NS, EXACT, MODE_INIT><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
         default:
             // the half-sweep dominates the run time: fixed-window instances for the
-            // paired path (exact view counts of at least 2)
+            // paired path (exact view counts of at least 2), in three tile shapes
             if constexpr (EXACT && NS >= 2) {
                 const int win = window_of(p);
                 if (win == 1) {
-                    pixel_kernel<NS, EXACT, MODE_SWEEP, 1><<<grid, BLOCK_THREADS, 0, stream>>>(p);
+                    launch_sweep_window<NS, EXACT, 1>(p, stream);
                     break;
                 }
                 if (win == 2) {
-                    pixel_kernel<NS, EXACT, MODE_SWEEP, 2><<<grid, BLOCK_THREADS, 0, stream>>>(p);
+                    launch_sweep_window<NS, EXACT, 2>(p, stream);
                     break;
                 }
             }

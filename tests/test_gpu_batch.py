@@ -81,6 +81,27 @@ def test_batch_equals_single_keyframe_runs(pm, ctx):
         assert np.array_equal(bc, sc) and np.array_equal(bd, sd) and np.array_equal(bn, sn)
 
 
+def test_tile_shapes_compute_the_same_numbers(pm, ctx):
+    """Every tile shape of the fixed-window half-sweeps (32x8, 64x4, 16x16) runs
+    the same per-pixel arithmetic, so the per-keyframe chains give bit-identical
+    maps whatever the shape; problems with other windows ignore the shape."""
+    probs = _problems()
+    args = [_args(p) for p in probs]
+    ref = None
+    for tile in (0, 1, 2):
+        batch = pm.Batch([(*a, p.params, None) for a, p in zip(args, probs)])
+        outs = [o.numpy() for o in pm.pmsp_densify_batch(ctx, batch, tuning=pm.pmsp_tuning(0, 0, 0, 1, tile))]
+        if ref is None:
+            ref = outs
+            continue
+        for (d0, n0, c0), (d1, n1, c1) in zip(ref, outs):
+            assert np.array_equal(d0, d1) and np.array_equal(n0, n1) and np.array_equal(c0, c1)
+    batch = pm.Batch([(*a, p.params, None) for a, p in zip(args[:1], probs[:1])])
+    with pytest.raises(pm.PmspError) as e:
+        pm.pmsp_densify_batch(ctx, batch, tuning=pm.pmsp_tuning(0, 0, 0, 1, 3))
+    assert e.value.code == pm.PMSP_EINVAL
+
+
 def test_batch_matches_oracle(pm, ctx):
     probs = _problems()[:3]
     args = [_args(p) for p in probs]
@@ -117,7 +138,7 @@ def test_autotune_returns_valid_setting(pm, ctx):
     args = [_args(p) for p in probs]
     batch = pm.Batch([(*a, dict(p.params, patch_stride=1, patch_w=7), None) for a, p in zip(args, probs)])
     t = pm.pmsp_autotune(ctx, batch, 0.01)
-    assert t.strategy in (0, 1) and t.order in (0, 1) and t.patch_stride in (0, 2)
+    assert t.strategy in (0, 1) and t.order in (0, 1) and t.patch_stride in (0, 2) and t.tile in (0, 1, 2)
     assert t.blocks_per_sm >= (1 if t.strategy == 0 else 0)
     outs = pm.pmsp_densify_batch(ctx, batch, 0, t)
     for o in outs:
