@@ -43,7 +43,9 @@
  *    (pmsp_view_filter, pmsp_fuse, pmsp_completeness). pmsp_sync waits for
  *    the stream and reports any error the kernels flagged.
  *  - Threads: a context is used by one host thread at a time, except the
- *    serving calls (submit/poll/wait), which are internally locked.
+ *    serving calls (ring_push/submit/poll/wait/get_serving_stats), which are
+ *    internally locked and may be made from different threads at once; the
+ *    last-error text then belongs to whichever call failed last.
  */
 #ifndef PMSP_H
 #define PMSP_H
@@ -416,7 +418,9 @@ typedef struct {
     const int64_t* src_frames;    /* n_src source frame ids */
     pmsp_params params;
     int32_t n_filter;             /* 0: no filter; else neighbour frame ids whose depth maps */
-    const int64_t* filter_frames; /*    (from finished requests) filter this result */
+    const int64_t* filter_frames; /*    (from finished requests) filter this result; the request
+                                     starts only once no running request has one of them, or its
+                                     own reference, as its reference or among its filter frames */
     float max_reproj_px;          /* filter threshold (pixels) */
     int32_t min_views;            /* filter: views that must agree */
 } pmsp_request;

@@ -157,7 +157,7 @@ static int build_plan(pmsp_ctx* c, BatchEngine& b, const pmsp_batch_item* items,
         for (int s = 0; s < it.n_src && !rc; ++s) {
             const pmsp_image& im = it.srcs[s];
             TexImage& ti = b.tex[TexKey(im.data, im.w, im.h, im.format, im.memory, im.pitch_bytes)];
-            rc = upload_texture(c, ti, &im);
+            rc = upload_texture(c, ti, &im, c->stream);
             tex[s] = ti.tex;
         }
         if (rc) break;

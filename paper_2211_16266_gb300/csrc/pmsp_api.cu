@@ -121,9 +121,9 @@ void free_texture(TexImage& t) {
 
 // Copy an image into a gather-capable texture (x wraps, y clamps, normalised
 // coordinates; uint8 reads as DN/255).
-int upload_texture(pmsp_ctx* c, TexImage& t, const pmsp_image* im) {
+int upload_texture(pmsp_ctx* c, TexImage& t, const pmsp_image* im, cudaStream_t st) {
     if (t.arr && (t.w != im->w || t.h != im->h || t.fmt != im->format)) {
-        cudaError_t e = cudaStreamSynchronize(c->stream);
+        cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(c, e, "sync before texture resize");
         free_texture(t);
     }
@@ -162,7 +162,7 @@ int upload_texture(pmsp_ctx* c, TexImage& t, const pmsp_image* im) {
     cudaError_t e = cudaMemcpy2DToArrayAsync(t.arr, 0, 0, im->data, im->pitch_bytes, row, im->h,
                                              im->memory == PMSP_HOST ? cudaMemcpyHostToDevice
                                                                      : cudaMemcpyDeviceToDevice,
-                                             c->stream);
+                                             st);
     if (e != cudaSuccess) return cuda_fail(c, e, "texture upload");
     return PMSP_OK;
 }
@@ -211,7 +211,7 @@ int prepare_problem(pmsp_ctx* c, const pmsp_image* ref, const pmsp_pose* ref_pos
     if ((int)c->src_tex.size() < n_src) c->src_tex.resize(n_src);
     cudaTextureObject_t tex[PMSP_MAX_SOURCES];
     for (int s = 0; s < n_src; ++s) {
-        if ((rc = upload_texture(c, c->src_tex[s], &srcs[s]))) return rc;
+        if ((rc = upload_texture(c, c->src_tex[s], &srcs[s], c->stream))) return rc;
         tex[s] = c->src_tex[s].tex;
     }
     const void* ref_dev = ref->data;
@@ -717,7 +717,7 @@ int pmsp_sample_bilinear(pmsp_ctx* c, const pmsp_image* img, int n, const float*
     if (rc) return rc;
     if (n < 0 || (n > 0 && (!uc || !vc || !out))) return ctx_fail(c, PMSP_EINVAL, "bad sample arrays");
     if (n == 0) return PMSP_OK;
-    if ((rc = upload_texture(c, c->sample_tex, img))) return rc;
+    if ((rc = upload_texture(c, c->sample_tex, img, c->stream))) return rc;
     const float *du = uc, *dv = vc;
     float* dout = out;
     if (img->memory == PMSP_HOST) {

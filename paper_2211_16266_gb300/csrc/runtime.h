@@ -37,7 +37,7 @@ int check_panorama(pmsp_ctx* c, const pmsp_image* im, const char* what);
 int check_params(pmsp_ctx* c, const pmsp_params* p, int n_src);
 int check_maps(pmsp_ctx* c, const pmsp_maps* m, int W, int H, bool need_normal, bool need_cost, const char* what);
 int ensure_buffer(pmsp_ctx* c, DevBuffer& b, size_t bytes);
-int upload_texture(pmsp_ctx* c, TexImage& t, const pmsp_image* im);
+int upload_texture(pmsp_ctx* c, TexImage& t, const pmsp_image* im, cudaStream_t st);
 void free_texture(TexImage& t);
 void compose_rel(const pmsp_pose& r, const pmsp_pose& s, double R[9], double t[3]);
 void fill_problem(PixelParams& P, const pmsp_image* ref, const void* ref_dev, int64_t ref_pitch,

@@ -223,13 +223,21 @@ int enqueue_request(Serving& s, Request* r, cudaStream_t st) {
     } else if (e == cudaSuccess) {
         e = cudaMemcpyAsync(filtered, base, N * 4, cudaMemcpyDeviceToDevice, st);
     }
-    RingFrame& ref = s.ring[r->ref];
-    if (e == cudaSuccess) {  // the ring's depth buffer was sized when the frame was pushed
-        e = cudaMemcpyAsync(ref.depth.ptr, base, N * 4, cudaMemcpyDeviceToDevice, st);
-        ref.has_depth = e == cudaSuccess;
-    }
+    // the ring's depth buffer was sized when the frame was pushed; it counts as the
+    // frame's depth map once the scheduler has seen this chain finish
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.ring[r->ref].depth.ptr, base, N * 4, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(r->done, st);
     return e == cudaSuccess ? PMSP_OK : PMSP_ECUDA;
+}
+
+// Whether starting r now would let two running chains touch one frame's depth
+// map at once: a chain writes its reference's map at its end and its filter
+// reads its neighbours' maps, on streams that are not ordered with each other.
+bool depth_conflict(const Serving& s, const Request* r) {
+    auto has = [](const std::vector<int>& v, int f) { return std::find(v.begin(), v.end(), f) != v.end(); };
+    for (const Request* q : s.running)
+        if (q->ref == r->ref || has(r->filters, q->ref) || has(q->filters, r->ref)) return true;
+    return false;
 }
 
 void scheduler(Serving* sp) {
@@ -248,6 +256,7 @@ void scheduler(Serving* sp) {
                 continue;
             }
             r->status = q == cudaSuccess ? DONE : FAILED;
+            if (q == cudaSuccess) s.ring[r->ref].has_depth = true;  // later filters may read it
             if (q != cudaSuccess) {
                 r->fail_code = late ? PMSP_ETIMEDOUT : PMSP_ECUDA;
                 s.err = late ? "request did not finish within the deadline" : cudaGetErrorString(q);
@@ -258,10 +267,12 @@ void scheduler(Serving* sp) {
             s.running.erase(s.running.begin() + k);
             s.cv_done.notify_all();
         }
-        // admission: FIFO while a lane is free, the maps fit and the resident work allows
+        // admission: FIFO while a lane is free, the maps fit, the resident work allows
+        // and no running chain writes or reads a depth map that this one reads or writes
         while (!s.queue.empty()) {
             Request* r = s.queue.front();
             if ((int)s.running.size() >= s.ctx->max_active) break;
+            if (depth_conflict(s, r)) break;
             if (s.bytes_in_use + r->bytes > s.ctx->mem_cap) break;
             if (s.running_tiles > 0 && s.running_tiles + r->tiles > tile_budget(s)) break;
             int lane = -1;
@@ -456,12 +467,7 @@ int pmsp_ring_push(pmsp_ctx* c, int64_t id, const pmsp_image* img, const pmsp_po
         e = cudaErrorMemoryAllocation;
     const cudaMemcpyKind k = img->memory == PMSP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (e == cudaSuccess) e = cudaMemcpy2DAsync(f.lin.ptr, row, img->data, img->pitch_bytes, row, img->h, k, s.upload);
-    if (e == cudaSuccess) {
-        const cudaStream_t saved = c->stream;
-        c->stream = s.upload;
-        rc = upload_texture(c, f.tex, img);
-        c->stream = saved;
-    }
+    if (e == cudaSuccess) rc = upload_texture(c, f.tex, img, s.upload);
     if (e == cudaSuccess && !rc) e = cudaEventRecord(s.upload_ev, s.upload);
     const bool ok = e == cudaSuccess && !rc && wait_event(s.upload_ev, STEP_DEADLINE_S);
     lk.lock();

@@ -159,3 +159,16 @@ def test_filter_against_finished_neighbours(pm):
                                              [fa[k][1] for k in (2, 3, 5, 6)], 1.0, 2)
         assert np.array_equal(out.depth, want)
         assert 0.2 < np.mean(out.depth > 0) < 1.0
+    # submitted together, the filtered request starts only after its neighbours have
+    # finished (their maps are written on other lanes), so the result is the same
+    with pm.Context(0, ring_capacity=16) as ctx:
+        _push(pm, ctx, fa, 0)
+        tickets = []
+        for k in (2, 3, 5, 6):
+            srcs_k = [j for j in range(k - 2, k + 3) if j != k and 0 <= j < 9]
+            tickets.append(pm.pmsp_submit(ctx, k, srcs_k, dict(PARAMS, keyframe_id=k)))
+        t = pm.pmsp_submit(ctx, 4, srcs, dict(PARAMS, keyframe_id=4), filter_frames=[2, 3, 5, 6])
+        for tk in tickets:
+            pm.pmsp_wait(ctx, tk, 60000, None)
+        out2 = pm.pmsp_wait(ctx, t, 60000, _maps(pm, 384, 192))
+        assert np.array_equal(out2.depth, want)
