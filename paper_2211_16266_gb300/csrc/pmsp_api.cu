@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -45,7 +46,10 @@ int ctx_fail(pmsp_ctx* c, int code, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    if (c) c->err = buf;
+    if (c) {
+        std::lock_guard<std::mutex> lk(c->err_mu);
+        memcpy(c->err, buf, sizeof buf);
+    }
     return code;
 }
 
@@ -408,7 +412,7 @@ int pmsp_destroy(pmsp_ctx* c) {
     return PMSP_OK;
 }
 
-const char* pmsp_last_error(pmsp_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+const char* pmsp_last_error(pmsp_ctx* c) { return c ? c->err : "NULL context"; }
 
 int pmsp_sync(pmsp_ctx* c) {
     if (!c) return PMSP_EINVAL;

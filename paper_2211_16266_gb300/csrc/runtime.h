@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -55,7 +56,11 @@ struct pmsp_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    std::string err;
+    // last error text: fixed storage (the pointer pmsp_last_error returns stays
+    // valid), written under err_mu because the serving calls may fail on
+    // different threads at once
+    char err[512] = {0};
+    std::mutex err_mu;
     unsigned* d_err = nullptr;  // device error word written by kernels
     uint64_t mem_cap = 0;
     int ring_capacity = 0;
