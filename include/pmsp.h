@@ -391,6 +391,8 @@ int pmsp_autotune(pmsp_ctx* ctx, const pmsp_batch_item* items, int n, float max_
  * Work is enqueued on the context's stream (the call returns once enqueued).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Descriptors travel in kernel parameters, so a call recorded into a graph
+ * reads no host memory when the graph is replayed.
  * All calls share the one array and each call resets it: calls whose work
  * overlaps on the GPU (different streams or contexts on one device) race, so
  * serialise them. PMSP_EINVAL for a batch above the limits or with host memory.

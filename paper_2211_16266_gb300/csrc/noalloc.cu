@@ -13,6 +13,7 @@
 // that loads the library keeps until the process exits.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -148,6 +149,21 @@ __global__ void __launch_bounds__(BLOCK_THREADS) noalloc_kernel(unsigned char* s
     }
 }
 
+// Descriptor bytes carried to the device in a kernel's parameters. A call
+// recorded into a graph then keeps them in the kernel node; a copy from the
+// host image on this function's stack would read that stack at every replay.
+constexpr int NA_CHUNK_WORDS = 1000;  // 4000 bytes, within the 4 KB classic parameter limit
+struct NaChunk {
+    unsigned words[NA_CHUNK_WORDS];
+};
+
+__global__ void noalloc_store(unsigned* dst, NaChunk chunk, int n_words) {
+    for (int k = threadIdx.x; k < n_words; k += blockDim.x) dst[k] = chunk.words[k];
+}
+
+static_assert(sizeof(LinearSrc) % 4 == 0 && sizeof(PixelParams) % 4 == 0, "descriptors are stored as words");
+static_assert((NA_OFF_LINEAR - NA_OFF_PREFIX) % 4 == 0, "tile offsets are stored as words");
+
 std::mutex g_setup_mu;
 void* g_scratch_addr[128];  // device address of the scratch array, per device ordinal
 bool g_scratch_ready[128];
@@ -233,12 +249,25 @@ extern "C" int pmsp_densify_batch_noalloc(pmsp_ctx* c, const pmsp_batch_item* it
     }
     prefix[n] = total;
 
-    // every call starts from zeroed counters and its own descriptors
-    cudaError_t e = cudaMemsetAsync(static_cast<unsigned char*>(scratch) + NA_OFF_COUNTERS, 0,
-                                    NA_MAX_PHASES * sizeof(unsigned), c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(static_cast<unsigned char*>(scratch) + NA_OFF_PREFIX, blob + NA_OFF_PREFIX,
-                            NA_USED - NA_OFF_PREFIX, cudaMemcpyHostToDevice, c->stream);
+    // every call starts from zeroed counters and its own descriptors: tile offsets
+    // and phase counts, then the n keyframes' sources and parameters
+    unsigned char* const dev = static_cast<unsigned char*>(scratch);
+    auto store = [&](size_t off, size_t bytes) {
+        cudaError_t err = cudaSuccess;
+        for (size_t done = 0; done < bytes && err == cudaSuccess; done += sizeof(NaChunk)) {
+            const size_t len = std::min(sizeof(NaChunk), bytes - done);
+            NaChunk ch;
+            memcpy(ch.words, blob + off + done, len);
+            noalloc_store<<<1, 256, 0, c->stream>>>(reinterpret_cast<unsigned*>(dev + off + done), ch,
+                                                    (int)(len / sizeof(unsigned)));
+            err = cudaGetLastError();
+        }
+        return err;
+    };
+    cudaError_t e = cudaMemsetAsync(dev + NA_OFF_COUNTERS, 0, NA_MAX_PHASES * sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = store(NA_OFF_PREFIX, NA_OFF_LINEAR - NA_OFF_PREFIX);
+    if (e == cudaSuccess) e = store(NA_OFF_LINEAR, (size_t)n * PMSP_MAX_SOURCES * sizeof(LinearSrc));
+    if (e == cudaSuccess) e = store(NA_OFF_PARAMS, (size_t)n * sizeof(PixelParams));
     if (e != cudaSuccess) return cuda_fail(c, e, "no-allocation descriptor upload");
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);

@@ -54,3 +54,35 @@ def test_noalloc_matches_batched_entry_point_twice():
         with pytest.raises(pm.PmspError) as e:
             pm.pmsp_densify_batch_noalloc(ctx, big)
         assert e.value.code == pm.PMSP_EINVAL
+
+
+def test_noalloc_recorded_in_a_graph_replays_the_same_maps():
+    """A call made while the context's stream is being recorded puts all of its
+    work into the graph, its descriptors included (nothing is read from host
+    memory at replay): every replay gives the maps of a direct call, bit for bit."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2211_16266_gb300 as pm
+
+    p = scenes.config1(W=256, H=128)
+    p.params = dict(p.params, iterations=3)
+    a = (_dev(p.ref.image), (p.ref.R, p.ref.t), [_dev(f.image) for f in p.srcs], [(f.R, f.t) for f in p.srcs])
+    s = torch.cuda.Stream()
+    with pm.Context(0, stream=s) as ctx:
+        batch = pm.Batch([(*a, p.params, None)])
+        pm.pmsp_densify_batch_noalloc(ctx, batch)   # the first call on a device, outside any capture
+        pm.pmsp_sync(ctx)
+        want = [x.copy() for x in batch.outs[0].numpy()]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            pm.pmsp_densify_batch_noalloc(ctx, batch)
+        out = batch.outs[0]
+        for x in (out.depth, out.normal, out.cost):
+            x.zero_()
+        for _ in range(2):
+            g.replay()
+            torch.cuda.synchronize()
+            for w, x in zip(want, out.numpy()):
+                assert np.array_equal(w, x)
+            out.depth.zero_()
