@@ -20,7 +20,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# PMSP_ORACLE_LIB names a prebuilt library to load instead of liboracle.so: the
+# planted-mistake tests point it at builds of oracle.c with one mistake planted.
+_PLANTED = os.environ.get("PMSP_ORACLE_LIB")
+_LIB = _PLANTED or os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 MAX_SRC = 16
@@ -28,6 +31,8 @@ MAX_SRC = 16
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so (gcc -O2, OpenMP)."""
+    if _PLANTED:
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])

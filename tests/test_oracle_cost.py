@@ -11,7 +11,9 @@ al.) for the patch cost without restating it (Sec. I, Sec. III-C). The pins:
 * affine intensity changes leave the cost unchanged, a negated source gives
   cost 2 for a view, best-k is the mean of the k smallest known view costs;
 * with zero translation the cost does not depend on the range;
-* ground-truth planes of a rendered room score far below random planes.
+* ground-truth planes of a rendered room score far below random planes, and
+  where the wall is seen obliquely they beat the fronto-parallel plane at the
+  same range (the slant acts only through each sample's range along its ray).
 """
 import math
 
@@ -192,3 +194,23 @@ def test_ground_truth_planes_beat_random_planes():
                          [(f.R.T, f.t) for f in prob.srcs], **prob.params)
     c_bad = bad.cost_map(gt, n_gt)
     assert np.mean(c_bad < 0.1) < 0.5
+
+
+def test_slanted_ground_truth_planes_beat_fronto_parallel_planes():
+    """A patch on a wall seen obliquely is explained by the wall's own plane, not by
+    the plane facing the camera at the same range: where the incidence cosine
+    |n . r_p| is at most 0.9, the ground-truth plane scores lower than the
+    fronto-parallel one (normal -r_p) on most pixels. The slant enters only through
+    the range of each patch sample along its own ray, t_q = d (n . r_p) / (n . r_q)."""
+    prob = scenes.config0()
+    pb = oracle.Problem.from_scene(prob)
+    gt = prob.ref.range
+    n_gt = _wall_normals_cam(prob, gt)
+    Hh, Ww = gt.shape
+    r = np.stack([oracle.bearing(Ww, Hh, u, v) for v in range(Hh) for u in range(Ww)])
+    r = r.reshape(Hh, Ww, 3).transpose(2, 0, 1)
+    slanted = -np.sum(n_gt * r, 0) <= 0.9
+    assert slanted.sum() > 0.3 * gt.size
+    c_gt = pb.cost_map(gt, n_gt)
+    c_fp = pb.cost_map(gt, -r)
+    assert np.mean(c_gt[slanted] < c_fp[slanted]) > 0.75

@@ -14,7 +14,10 @@ reads this as a forward-backward reprojection test (error < 1 px in at least
   same for any positive ranges, and under a yaw by whole pixels (the nearest
   pixel is the exact ray) every pixel agrees;
 * a zero range (no data) in the neighbour never agrees; a zero reference
-  range stays zero.
+  range stays zero;
+* rolling the reference map by k columns with its camera yawed by k pixels
+  rolls every decision with it, also where the roll brings a pixel to the
+  seam (the longitude error is wrapped to half a panorama).
 """
 import numpy as np
 
@@ -106,3 +109,27 @@ def test_min_views_threshold():
     for k in (1, 2, 3, 4):
         out, _, _ = oracle.consistency_filter(Dr, (Rr, tr), Ds, Ps, 1.0, k)
         assert np.array_equal(out > 0, agree >= k)
+
+
+def test_decisions_follow_a_yaw_of_the_reference_across_the_seam():
+    """Rolling the reference map by k columns while yawing its camera by k pixels
+    (R' = Ry R, t' = Ry t with Ry turning longitude by 2 pi k / W) is the same
+    physical map, so the agreeing-view counts roll with it, also for the pixels
+    that the roll moves next to the seam. A neighbour at half the resolution
+    makes round-trip errors of 0.5 to 1 px common, and those cross the seam at
+    column 0 or W - 1 for some k."""
+    W, H = 64, 32
+    ref = _frames(W, H)[2]
+    low = _frames(W // 2, H // 2)
+    nb = [low[i] for i in (0, 1, 3, 4)]
+    Rr, tr, Dr = ref
+    kw = dict(nbr_depths=[d for _, _, d in nb], nbr_poses=[(R, t) for R, t, _ in nb], max_px=1.0, min_views=2)
+    _, agree0, mg0 = oracle.consistency_filter(Dr, (Rr, tr), **kw)
+    assert np.mean(agree0 > 0) > 0.5
+    for k in range(1, W):
+        a = 2 * np.pi * k / W
+        Ry = np.array([[np.cos(a), 0, np.sin(a)], [0, 1, 0], [-np.sin(a), 0, np.cos(a)]])
+        assert np.allclose(Ry @ oracle.bearing(W, H, 3, 7), oracle.bearing(W, H, 3 + k, 7), atol=1e-12)
+        _, agree_k, mg_k = oracle.consistency_filter(np.roll(Dr, k, axis=1), (Ry @ Rr, Ry @ tr), **kw)
+        clear = (np.roll(mg0, k, axis=1) > 1e-9) & (mg_k > 1e-9)
+        assert np.array_equal(np.roll(agree0, k, axis=1)[clear], agree_k[clear]), k

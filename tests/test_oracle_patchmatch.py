@@ -14,7 +14,9 @@ the cost it minimises is pinned in test_oracle_cost.py. Here:
   numpy's Philox;
 * brute force: an exhaustive plane sweep on a tiny panorama does not beat the
   PatchMatch result by more than a small margin on almost all pixels;
-* on the rendered 256x128 room the result matches ground-truth range.
+* on the rendered 256x128 room the result matches ground-truth range;
+* the state never leaves the search space (ranges in [d_min, d_max], unit
+  normals facing the camera) even when the true surface lies outside it.
 """
 import math
 
@@ -203,3 +205,28 @@ def test_config0_matches_ground_truth():
     assert np.mean(rel < 0.05) > 0.9
     assert np.mean(rel < 0.01) > 0.5
     assert np.median(c) < 0.02
+
+
+def test_state_stays_in_the_search_space():
+    """The search space of Sec. III-B/C is ranges in [d_min, d_max] and unit normals
+    facing the camera; propagation re-intersections and refinement proposals that
+    leave it are not taken. A range window narrower than the room (part of the true
+    surface lies beyond d_max) makes out-of-window candidates the better fit, so a
+    missing bound would show."""
+    W, H = 48, 24
+    scene = scenes.Scene(seed=1234)
+    C = np.array([0.2, 0.1, -0.3])
+    R0, t0 = scenes.pose_from_centre(scenes.rot_y(0.3), C)
+    views = [scenes.pose_from_centre(scenes.rot_y(0.3), C + np.array(o)) for o in ((0.2, 0, 0), (0, 0, 0.2))]
+    img0, rng0 = scene.render(R0, t0, W, H)
+    imgs = [scene.render(R, t, W, H)[0] / 255.0 for R, t in views]
+    d_min, d_max = 0.5, 2.0
+    assert np.mean(rng0 > d_max) > 0.2
+    pb = oracle.Problem(img0 / 255.0, (R0, t0), imgs, views, d_min=d_min, d_max=d_max, patch_w=7,
+                        patch_stride=1, iterations=6, best_k=1)
+    d, n, c = pb.densify()
+    assert np.all((d >= d_min * (1 - 1e-12)) & (d <= d_max * (1 + 1e-12)))
+    assert np.allclose(np.sum(n * n, 0), 1.0, atol=1e-12)
+    r = np.stack([oracle.bearing(W, H, u, v) for v in range(H) for u in range(W)]).reshape(H, W, 3)
+    assert np.all(np.sum(n * r.transpose(2, 0, 1), 0) < 0)
+    assert np.array_equal(c, pb.cost_map(d, n))
