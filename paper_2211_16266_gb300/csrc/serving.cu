@@ -25,6 +25,7 @@
 #include "common.cuh"
 #include "pmsp.h"
 #include "runtime.h"
+#include "serving_policy.h"
 
 namespace pmsp {
 
@@ -134,12 +135,6 @@ int dev_alloc(DevBuffer& b, size_t bytes, cudaStream_t st) {
     return PMSP_OK;
 }
 
-// Tiles of resident work admission aims for: about two waves of six resident
-// 128-thread blocks per SM (the sweep kernels keep 4 to 7). More would only
-// stretch every running request's latency; a request that alone exceeds it
-// still runs.
-size_t tile_budget(const Serving& s) { return (size_t)s.sms * 6 * 2; }
-
 // Give back a request's frames and maps (stream-ordered free: no device-wide sync).
 void release_request(Serving& s, Request* r) {
     for (int f : r->srcs) s.ring[f].pins--;
@@ -230,14 +225,15 @@ int enqueue_request(Serving& s, Request* r, cudaStream_t st) {
     return e == cudaSuccess ? PMSP_OK : PMSP_ECUDA;
 }
 
+DepthUse depth_use(const Request* r) { return DepthUse{r->ref, r->filters.data(), (int)r->filters.size()}; }
+
 // Whether starting r now would let two running chains touch one frame's depth
-// map at once: a chain writes its reference's map at its end and its filter
-// reads its neighbours' maps, on streams that are not ordered with each other.
-bool depth_conflict(const Serving& s, const Request* r) {
-    auto has = [](const std::vector<int>& v, int f) { return std::find(v.begin(), v.end(), f) != v.end(); };
-    for (const Request* q : s.running)
-        if (q->ref == r->ref || has(r->filters, q->ref) || has(q->filters, r->ref)) return true;
-    return false;
+// map at once (serving_policy.h).
+bool conflicts_with_running(const Serving& s, const Request* r) {
+    std::vector<DepthUse> running;
+    running.reserve(s.running.size());
+    for (const Request* q : s.running) running.push_back(depth_use(q));
+    return depth_conflict(depth_use(r), running.data(), (int)running.size());
 }
 
 void scheduler(Serving* sp) {
@@ -271,10 +267,9 @@ void scheduler(Serving* sp) {
         // and no running chain writes or reads a depth map that this one reads or writes
         while (!s.queue.empty()) {
             Request* r = s.queue.front();
-            if ((int)s.running.size() >= s.ctx->max_active) break;
-            if (depth_conflict(s, r)) break;
-            if (s.bytes_in_use + r->bytes > s.ctx->mem_cap) break;
-            if (s.running_tiles > 0 && s.running_tiles + r->tiles > tile_budget(s)) break;
+            const AdmitState st{(int)s.running.size(), s.ctx->max_active, s.bytes_in_use, s.ctx->mem_cap,
+                                s.running_tiles, serving_tile_budget(s.sms)};
+            if (admit_block(st, r->bytes, r->tiles, conflicts_with_running(s, r)) != ADMIT_OK) break;
             int lane = -1;
             for (int i = 0; i < (int)s.lanes.size() && lane < 0; ++i)
                 if (!s.lane_req[i]) lane = i;
@@ -422,14 +417,11 @@ int pmsp_ring_push(pmsp_ctx* c, int64_t id, const pmsp_image* img, const pmsp_po
     std::unique_lock<std::mutex> lk(s.mu);
     int slot = find_frame(s, id);
     if (slot >= 0 && s.ring[slot].pins > 0) return ctx_fail(c, PMSP_EBUSY, "frame %lld is in use", (long long)id);
-    if (slot < 0) {
-        for (int i = 0; i < (int)s.ring.size() && slot < 0; ++i)
-            if (!s.ring[i].used && !s.ring[i].loading) slot = i;
-        if (slot < 0) {  // evict the oldest unused frame
-            uint64_t best = UINT64_MAX;
-            for (int i = 0; i < (int)s.ring.size(); ++i)
-                if (s.ring[i].pins == 0 && s.ring[i].seq < best) best = s.ring[i].seq, slot = i;
-        }
+    if (slot < 0) {  // a free slot, else evict the oldest frame no request holds
+        std::vector<SlotView> view(s.ring.size());
+        for (size_t i = 0; i < s.ring.size(); ++i)
+            view[i] = SlotView{s.ring[i].used, s.ring[i].loading, s.ring[i].pins, s.ring[i].seq};
+        slot = ring_pick_slot(view.data(), (int)view.size());
         if (slot < 0) return ctx_fail(c, PMSP_EBUSY, "every ring frame is used by a request");
     }
     // Claim the slot: nothing uses an unpinned frame, so it is rewritten while
