@@ -267,9 +267,9 @@ void scheduler(Serving* sp) {
         // and no running chain writes or reads a depth map that this one reads or writes
         while (!s.queue.empty()) {
             Request* r = s.queue.front();
-            const AdmitState st{(int)s.running.size(), s.ctx->max_active, s.bytes_in_use, s.ctx->mem_cap,
-                                s.running_tiles, serving_tile_budget(s.sms)};
-            if (admit_block(st, r->bytes, r->tiles, conflicts_with_running(s, r)) != ADMIT_OK) break;
+            const AdmitState now{(int)s.running.size(), s.ctx->max_active, s.bytes_in_use, s.ctx->mem_cap,
+                                 s.running_tiles, serving_tile_budget(s.sms)};
+            if (admit_block(now, r->bytes, r->tiles, conflicts_with_running(s, r)) != ADMIT_OK) break;
             int lane = -1;
             for (int i = 0; i < (int)s.lanes.size() && lane < 0; ++i)
                 if (!s.lane_req[i]) lane = i;
