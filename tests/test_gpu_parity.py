@@ -60,6 +60,15 @@ def _problem(name):
         p2 = scenes.trajectory_problem(384, 192, 6, fmt="f16")
         p2.params = p.params
         return p2
+    if name == "max16":
+        # the largest view count and window: 16 sources (the guarded 16-view kernel),
+        # 21x21 window sampled densely (441 samples, rows clamped at both poles),
+        # best-k = S, on a panorama of ragged tiles
+        p = scenes.trajectory_problem(48, 24, 16, seed_scene=1013)
+        p.params = dict(d_min=0.3, d_max=10.0, patch_w=21, patch_stride=1, iterations=2, best_k=16,
+                        sigma_color=0.2, sigma_space=6.0, n_refine=6, neighbor_table=0, seed=11,
+                        keyframe_id=5)
+        return p
     if name == "tiny":
         p = scenes.trajectory_problem(8, 4, 1, seed_scene=1011)
         p.params = dict(d_min=0.3, d_max=10.0, patch_w=5, patch_stride=1, iterations=2, best_k=1,
@@ -103,7 +112,7 @@ def test_bilinear_sample_matches_oracle(pm, ctx, fmt):
 
 # ---------------------------------------------------------------------- cost
 
-@pytest.mark.parametrize("name", ["c0", "mid6", "ragged", "mid6_f16", "tiny"])
+@pytest.mark.parametrize("name", ["c0", "mid6", "ragged", "mid6_f16", "tiny", "max16"])
 def test_cost_of_given_planes(pm, ctx, name):
     prob = _problem(name)
     pb = oracle.Problem.from_scene(prob)
@@ -134,7 +143,7 @@ def test_cost_of_given_planes(pm, ctx, name):
 
 # ---------------------------------------------------------------------- init
 
-@pytest.mark.parametrize("name", ["c0", "mid6", "ragged"])
+@pytest.mark.parametrize("name", ["c0", "mid6", "ragged", "max16"])
 def test_random_init(pm, ctx, name):
     prob = _problem(name)
     pb = oracle.Problem.from_scene(prob)
@@ -149,7 +158,7 @@ def test_random_init(pm, ctx, name):
 
 # ---------------------------------------------------------------- half-sweep
 
-@pytest.mark.parametrize("name", ["c0", "mid6", "ragged", "tiny"])
+@pytest.mark.parametrize("name", ["c0", "mid6", "ragged", "tiny", "max16"])
 def test_one_halfsweep_from_shared_state(pm, ctx, name):
     prob = _problem(name)
     pb = oracle.Problem.from_scene(prob)
