@@ -81,6 +81,31 @@ def test_batch_equals_single_keyframe_runs(pm, ctx):
         assert np.array_equal(bc, sc) and np.array_equal(bd, sd) and np.array_equal(bn, sn)
 
 
+def test_batch_with_more_than_ten_sources(pm, ctx):
+    """A batch whose largest view count is above 10 runs the guarded 16-view
+    instance of the persistent kernel (and of the per-keyframe chains): it
+    matches the single-keyframe runs within the parity tolerance, and the chains
+    bit for bit."""
+    pa = scenes.trajectory_problem(96, 48, 12, seed_scene=1014)
+    pa.params = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=2, best_k=4, sigma_color=0.2,
+                     sigma_space=3.0, n_refine=6, neighbor_table=0, seed=3, keyframe_id=21)
+    pb = scenes.trajectory_problem(64, 32, 4, seed_scene=1015)
+    pb.params = dict(pa.params, best_k=2, keyframe_id=22)
+    probs = [pa, pb]
+    args = [_args(p) for p in probs]
+    singles = [pm.pmsp_densify(ctx, *a, p.params).numpy() for a, p in zip(args, probs)]
+    for strategy in (0, 1):
+        batch = pm.Batch([(*a, p.params, None) for a, p in zip(args, probs)])
+        outs = pm.pmsp_densify_batch(ctx, batch, tuning=pm.pmsp_tuning(0, 0, 0, strategy))
+        for (sd, sn, sc), o in zip(singles, outs):
+            bd, bn, bc = o.numpy()
+            if strategy == 0:
+                assert np.mean(np.abs(bc - sc) <= 1e-4) >= 0.995
+                assert np.mean(np.abs(bd - sd) <= 5e-3 * sd) >= 0.995
+            else:
+                assert np.array_equal(bc, sc) and np.array_equal(bd, sd) and np.array_equal(bn, sn)
+
+
 def test_tile_shapes_compute_the_same_numbers(pm, ctx):
     """Every tile shape of the fixed-window half-sweeps (32x8, 64x4, 16x16) runs
     the same per-pixel arithmetic, so the per-keyframe chains give bit-identical
