@@ -9,9 +9,9 @@ the cost it minimises is pinned in test_oracle_cost.py. Here:
   wall (closed form: a plane through the neighbour's wall point);
 * a half-sweep equals independent per-pixel updates (order independence) and
   never raises a pixel's cost; the stored cost is the cost of the stored plane;
-* the random initial planes come from Philox blocks laid out as
-  (pixel, iteration, stage, 0) under key (seed, keyframe id), checked with
-  numpy's Philox;
+* the random initial planes and the refinement proposals come from Philox
+  blocks laid out as (pixel, iteration, stage, 0) under key (seed, keyframe
+  id), one uniform per perturbed component, checked with numpy's Philox;
 * brute force: an exhaustive plane sweep on a tiny panorama does not beat the
   PatchMatch result by more than a small margin on almost all pixels;
 * on the rendered 256x128 room the result matches ground-truth range;
@@ -230,3 +230,54 @@ def test_state_stays_in_the_search_space():
     r = np.stack([oracle.bearing(W, H, u, v) for v in range(H) for u in range(W)]).reshape(H, W, 3)
     assert np.all(np.sum(n * r.transpose(2, 0, 1), 0) < 0)
     assert np.array_equal(c, pb.cost_map(d, n))
+
+
+def _philox_block(seed, keyframe_id, counter):
+    """The Philox4x64-10 block at a 256-bit counter, from numpy's generator (which
+    advances its counter before each block, so it is started one below)."""
+    c = (sum(int(w) << (64 * i) for i, w in enumerate(counter)) - 1) % (1 << 256)
+    ctr = np.array([(c >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
+    return np.random.Philox(key=np.array([seed, keyframe_id], dtype=np.uint64), counter=ctr).random_raw(4)
+
+
+def test_refinement_draw_layout():
+    """With the incumbent's cost above any cost (5 > 2) and every neighbour plane facing
+    away (never re-intersected), the first refinement test of a half-sweep is always
+    taken, so one test exposes its proposal: the range and normal perturbations of
+    Sec. III-C built from the Philox block at counter (pixel, iteration, 1, 0) under key
+    (seed, keyframe id), checked with numpy's Philox, one uniform per component."""
+    W, H, seed, kf, it, colour = 64, 32, 13, 4, 2, 1
+    scene = scenes.Scene(seed=1234)
+    C = np.array([0.2, 0.1, -0.3])
+    R0, t0 = scenes.pose_from_centre(scenes.rot_y(0.3), C)
+    R1, t1 = scenes.pose_from_centre(scenes.rot_y(0.3), C + np.array([0.2, 0.0, 0.0]))
+    img0, _ = scene.render(R0, t0, W, H)
+    img1, _ = scene.render(R1, t1, W, H)
+    d_min, d_max = 0.3, 10.0
+    pb = oracle.Problem(img0 / 255.0, (R0, t0), [img1 / 255.0], [(R1, t1)], d_min=d_min, d_max=d_max, patch_w=5,
+                        patch_stride=1, iterations=1, best_k=1, n_refine=1, seed=seed, keyframe_id=kf)
+    r = np.stack([oracle.bearing(W, H, u, v) for v in range(H) for u in range(W)], 1).reshape(3, H, W)
+    rng = np.random.default_rng(1)
+    d0 = rng.uniform(0.5, 5.0, (H, W))
+    n0 = -r + 0.3 * rng.normal(size=(3, H, W))
+    n0 /= np.linalg.norm(n0, axis=0)
+    n0 = np.where(np.sum(n0 * r, 0) < 0, n0, -n0)
+    other = ((np.arange(W)[None, :] + np.arange(H)[:, None]) % 2) != colour
+    n0[:, other] = r[:, other]
+    d, n, c = d0.copy(), np.ascontiguousarray(n0).copy(), np.full((H, W), 5.0)
+    pb.halfsweep(d, n, c, colour, it)
+    for (u, v) in [(1, 0), (0, 1), (W - 1, 0), (17, 8), (40, 15), (33, 30), (W - 2, H - 1)]:
+        assert (u + v) % 2 == colour
+        p = v * W + u
+        uu = [(int(x) >> 40) / 2**24 for x in _philox_block(seed, kf, [p, it, 1, 0])]
+        s = 0.5
+        inv = 1 / d0[v, u] + (2 * uu[0] - 1) * s * (1 / d_min - 1 / d_max)
+        inv = min(max(inv, 1 / d_max), 1 / d_min)
+        assert abs(d[v, u] - 1 / inv) <= 1e-12 * d[v, u]
+        m = n0[:, v, u] + s * (2 * np.array(uu[1:]) - 1)
+        m /= np.linalg.norm(m)
+        cr = m @ r[:, v, u]
+        m = -r[:, v, u] if abs(cr) < 1e-3 else (-m if cr > 0 else m)
+        assert np.allclose(n[:, v, u], m, atol=1e-12, rtol=0)
+        assert c[v, u] <= 2.0
+    assert np.array_equal(d[other], d0[other])

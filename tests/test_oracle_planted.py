@@ -8,14 +8,10 @@ least one pin must fail. The unplanted oracle passes the same modules in the
 rest of the suite. A case whose snippet no longer occurs once in oracle.c
 fails, so the list follows the source.
 
-Slips the oracle pins alone do not catch, and why:
-* which uniform of a refinement draw perturbs which normal component (the
-  components are exchangeable; the assignment is a convention of the
-  Philox draw layout, fixed against the independent CUDA restatement by the
-  GPU parity of one half-sweep from a shared state);
-* wrapping versus clamping the nearest pixel's column in the completeness
-  splat (rounding a projection, which lies in [-0.5, W - 0.5), never leaves
-  [0, W - 1], so both read the same pixel).
+One slip no pin can catch, because it cannot change a result: wrapping
+versus clamping the nearest pixel's column in the completeness splat
+(rounding a projection, which lies in [-0.5, W - 0.5), never leaves
+[0, W - 1]).
 """
 import os
 import subprocess
@@ -50,6 +46,9 @@ PLANTED = [
      "double lon = 2.0 * ORC_PI * u / W - ORC_PI;", CAMERA),
     ("sample_weights_swapped", "return (1.0 - fy) * ((1.0 - fx) * t00 + fx * t10)",
      "return (1.0 - fy) * (fx * t00 + (1.0 - fx) * t10)", CAMERA),
+    ("bearing_z_without_cos_lat", "r[2] = cos(lat) * cos(lon);", "r[2] = cos(lon);", CAMERA),
+    ("sample_rows_wrapped", "y1 = clamp_i(j0 + 1, 0, im->H - 1);", "y1 = wrap_i(j0 + 1, im->H);", CAMERA),
+    ("rel_pose_translation_sign", "out->t[i] = s->t[i] - acc;", "out->t[i] = s->t[i] + acc;", CAMERA),
     ("rel_pose_transposed", "acc += s->R[3 * i + k] * r->R[3 * j + k];",
      "acc += s->R[3 * i + k] * r->R[3 * k + j];", CAMERA),
     # random numbers
@@ -62,6 +61,10 @@ PLANTED = [
     ("ncc_variance_uses_wrong_sum", "double varJ = sw[s] * sJJ[s] - sJ[s] * sJ[s];",
      "double varJ = sw[s] * sJJ[s] - sI[s] * sJ[s];", COST),
     ("spatial_weight_dy_dropped", "e += (double)(ox * ox + oy * oy)", "e += (double)(ox * ox)", COST),
+    ("colour_weight_not_squared", "e += (Iq - Ip) * (Iq - Ip) / (2.0 * p->sigma_color * p->sigma_color);",
+     "e += (Iq - Ip) / (2.0 * p->sigma_color * p->sigma_color);", COST),
+    ("weight_sum_unweighted", "sw[s] += w;", "sw[s] += 1.0;", COST),
+    ("ncc_scaled", "double ncc = cov / sqrt(varI * varJ);", "double ncc = cov / sqrt(varI * varJ) * 0.999;", COST),
     ("colour_weight_sign", "double w = exp(-e);", "double w = exp(e);", COST),
     ("plane_ray_ratio_inverted", "double tq = d * ndotrp / denom;", "double tq = d * denom / ndotrp;", COST),
     ("best_k_takes_largest", "if (!used[s] && (best < 0 || c[s] < c[best])) best = s;",
@@ -80,6 +83,7 @@ PLANTED = [
     # initialisation and propagation (Sec. III-B, III-C)
     ("init_uniform_in_range", "double inv = 1.0 / p->d_max + r[0] * (1.0 / p->d_min - 1.0 / p->d_max);",
      "double inv = 1.0 / (p->d_min + r[0] * (p->d_max - p->d_min));", PM),
+    ("init_normal_y_from_cosine", "n[1] = rho * sin(phi);", "n[1] = rho * cos(phi);", PM),
     ("init_normal_hemisphere", "double z = 1.0 - 2.0 * r[1], phi", "double z = 1.0 - r[1], phi", PM),
     ("face_camera_sign", "} else if (c > 0) {", "} else if (c < 0) {", COST + PM),
     ("neighbours_same_colour", "static const int t0[16] = {0, -3, 0, 3, -3, 0, 3, 0,",
@@ -93,6 +97,11 @@ PLANTED = [
      "if (!(den > 1e-6)) continue;\n        double dc", PM),
     ("refine_normal_not_renormalised", "nc[0] /= len; nc[1] /= len; nc[2] /= len;", "(void)len;", PM),
     ("refine_range_not_clamped", "if (inv < inv_lo) inv = inv_lo;", "", PM),
+    ("propagation_rows_clamped", "if (qv < 0 || qv >= H) continue;\n        int qu",
+     "if (qv < 0 || qv >= H) qv = clamp_i(qv, 0, H - 1);\n        int qu", PM),
+    ("refine_draws_init_stage", "draw4(p, (uint64_t)i, (uint64_t)iter, (uint64_t)(1 + k), r);",
+     "draw4(p, (uint64_t)i, (uint64_t)iter, (uint64_t)k, r);", PM),
+    ("refine_normal_y_from_x_draw", "bn[1] + s * (2.0 * r[2] - 1.0)", "bn[1] + s * (2.0 * r[1] - 1.0)", PM),
     ("halfsweep_colour_ignores_row", "for (int u = (v + colour) & 1; u < W; u += 2)",
      "for (int u = colour; u < W; u += 2)", PM),
     ("refine_range_not_halved", "double s = ldexp(1.0, -(k + 1));", "double s = 1.0;", PM),
@@ -106,6 +115,9 @@ PLANTED = [
      "orc_rel_pose(&pose_j[j], pose_r, &rel_f[j]);", FILTER),
     ("filter_floor_not_nearest", "double fu = floor(uc + 0.5), fv = floor(vc + 0.5);\n                    double m1",
      "double fu = floor(uc), fv = floor(vc);\n                    double m1", FILTER),
+    ("filter_zero_neighbour_range_used", "if (!(dj > 0)) continue;", "if (dj < 0) continue;", FILTER),
+    ("filter_neighbour_bearing_from_reference_grid", "orc_bearing(Wj[j], Hj[j], ui, vi, rq);",
+     "orc_bearing(W, H, ui, vi, rq);", FILTER),
     ("filter_back_projection_forward_pose", "apply_pose(&rel_b[j], Xj, Z);", "apply_pose(&rel_f[j], Xj, Z);",
      FILTER),
     # plane-map warping (Sec. III-B)
@@ -118,6 +130,9 @@ PLANTED = [
      "double fu = floor(uc), fv = floor(vc);\n            int qu", WARP),
     ("warp_plane_ignored", "if (!used) orc_random_plane(pb, u, v, &d, n);", "orc_random_plane(pb, u, v, &d, n);",
      WARP),
+    ("warp_normal_not_rotated",
+     "n[a] = rel->R[3 * a] * nj[0] + rel->R[3 * a + 1] * nj[1] + rel->R[3 * a + 2] * nj[2];",
+     "n[a] = nj[a];", WARP),
     ("warp_plane_offset_from_own_ray", "d = dot3(n, Y) / den;", "d = sqrt(dot3(Y, Y));", WARP),
     # median post-filter (Sec. III-C)
     ("median_upper", "m = win[(n - 1) / 2];", "m = win[n / 2];", MEDIAN),
@@ -126,6 +141,8 @@ PLANTED = [
     ("median_threshold_inclusive", "out[i] = diff > lim ? 0.0 : d;", "out[i] = diff >= lim ? 0.0 : d;", MEDIAN),
     ("median_seam_clamped", "double x = depth[(size_t)y * W + wrap_i(u + dx, W)];",
      "double x = depth[(size_t)y * W + clamp_i(u + dx, 0, W - 1)];", MEDIAN),
+    ("median_window_short", "for (int dy = -r; dy <= r; ++dy) {", "for (int dy = -r; dy < r; ++dy) {", MEDIAN),
+    ("median_counts_holes", "if (x > 0) win[n++] = x;", "win[n++] = x;", MEDIAN),
     ("median_threshold_absolute", "lim = tau32 * m32;", "lim = tau32;", MEDIAN),
     # View Filter (Sec. III-A, Eq. 1)
     ("view_share_inclusive", "return f > min_frac;", "return f >= min_frac;", VIEW),
@@ -133,6 +150,7 @@ PLANTED = [
      "ca[k] = -(A->R[k] * A->t[0] + A->R[3 + k] * A->t[1] + A->R[6 + k] * A->t[2]);",
      "ca[k] = -(A->R[3 * k] * A->t[0] + A->R[3 * k + 1] * A->t[1] + A->R[3 * k + 2] * A->t[2]);", VIEW),
     ("view_cosine_wrong_norm", "double c = dot3(a, b) / (la * lb);", "double c = dot3(a, b) / (la * la);", VIEW),
+    ("view_lower_bound_dropped", "ok = th >= min_deg && th <= max_deg;", "ok = th <= max_deg;", VIEW),
     ("view_half_angle", "th = acos(c) * (180.0 / ORC_PI);", "th = acos(c) * (90.0 / ORC_PI);", VIEW),
     # fusion and completeness (Sec. III, IV)
     ("fuse_truncates_keys", "double q = X[a] / voxel, f = floor(q);", "double q = X[a] / voxel, f = trunc(q);",
@@ -144,6 +162,14 @@ PLANTED = [
     ("fuse_duplicates_by_two_keys",
      "if (j > 0 && v[j].k[0] == v[j - 1].k[0] && v[j].k[1] == v[j - 1].k[1] && v[j].k[2] == v[j - 1].k[2])",
      "if (j > 0 && v[j].k[0] == v[j - 1].k[0] && v[j].k[1] == v[j - 1].k[1])", FUSION),
+    ("fuse_holes_kept", "            if (!(d > 0)) {\n                if (margin)",
+     "            if (d < 0) {\n                if (margin)", FUSION),
+    ("fuse_translation_sign",
+     "for (int a = 0; a < 3; ++a) Xc[a] = d * r[a] - P->t[a];\n            for (int a = 0; a < 3; ++a) X[a]",
+     "for (int a = 0; a < 3; ++a) Xc[a] = d * r[a] + P->t[a];\n            for (int a = 0; a < 3; ++a) X[a]",
+     FUSION),
+    ("completeness_pose_ignored", "apply_pose(pose, pts + 3 * i, Y);",
+     "Y[0] = pts[3 * i]; Y[1] = pts[3 * i + 1]; Y[2] = pts[3 * i + 2];", FUSION),
     ("fuse_keeps_last", "return (x->order > y->order) - (x->order < y->order);",
      "return (x->order < y->order) - (x->order > y->order);", FUSION),
     ("completeness_denominator", "return (double)c / ((double)W * H);", "return (double)c / ((double)W * H + W);",
