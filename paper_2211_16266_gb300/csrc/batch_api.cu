@@ -42,6 +42,7 @@ struct BatchEngine {
     void* h_problems = nullptr;  // pinned copies read by the captured graph
     void* h_work = nullptr;
     size_t h_problems_bytes = 0, h_work_bytes = 0;
+    cudaEvent_t staged_ev = nullptr;  // recorded after the last eager read of the pinned copies
     cudaStream_t capture = nullptr;
     std::vector<cudaStream_t> branch;  // per-keyframe launch chains (strategy 1)
     std::vector<cudaEvent_t> join_ev;
@@ -108,6 +109,7 @@ void batch_shutdown(pmsp_ctx* c) {
     for (cudaStream_t x : b.branch) cudaStreamDestroy(x);
     for (cudaEvent_t x : b.join_ev) cudaEventDestroy(x);
     if (b.fork_ev) cudaEventDestroy(b.fork_ev);
+    if (b.staged_ev) cudaEventDestroy(b.staged_ev);
     delete c->batch;
     c->batch = nullptr;
 }
@@ -238,8 +240,18 @@ static int build_plan(pmsp_ctx* c, BatchEngine& b, const pmsp_batch_item* items,
     return PMSP_OK;
 }
 
-static int ensure_pinned(pmsp_ctx* c, void*& p, size_t& have, size_t need) {
+// Wait until the last eager read of the pinned plan copies has run (the event is
+// created on first use; an event never recorded counts as complete).
+static int wait_staged(pmsp_ctx* c, BatchEngine& b) {
+    const cudaError_t e = b.staged_ev ? cudaEventSynchronize(b.staged_ev)
+                                      : cudaEventCreateWithFlags(&b.staged_ev, cudaEventDisableTiming);
+    return e == cudaSuccess ? PMSP_OK : cuda_fail(c, e, "batch staging wait");
+}
+
+static int ensure_pinned(pmsp_ctx* c, BatchEngine& b, void*& p, size_t& have, size_t need) {
     if (have >= need) return PMSP_OK;
+    int rc;
+    if (p && (rc = wait_staged(c, b))) return rc;  // a queued copy may still read the old buffer
     if (p) cudaFreeHost(p);
     p = nullptr;
     have = 0;
@@ -299,13 +311,21 @@ static int enqueue_plan(pmsp_ctx* c, BatchEngine& b, const BatchPlan& plan, cons
     if ((rc = ensure_buffer(c, b.d_problems, pb)) || (rc = ensure_buffer(c, b.d_work, wb)) ||
         (rc = ensure_buffer(c, b.d_counters, (size_t)std::max(phases, 1) * sizeof(unsigned))))
         return rc;
-    if ((rc = ensure_pinned(c, b.h_problems, b.h_problems_bytes, pb)) ||
-        (rc = ensure_pinned(c, b.h_work, b.h_work_bytes, wb)))
+    if ((rc = ensure_pinned(c, b, b.h_problems, b.h_problems_bytes, pb)) ||
+        (rc = ensure_pinned(c, b, b.h_work, b.h_work_bytes, wb)))
         return rc;
+    // The pinned copies are rewritten below, and stream order does not cover host
+    // writes: outside a capture, wait until the last eager read of them (an earlier
+    // call's upload or graph replay, possibly still queued) has run. A capture only
+    // records the read; its replays are followed by that wait in the next eager call.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool eager = cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+    if (eager && (rc = wait_staged(c, b))) return rc;
     memcpy(b.h_problems, plan.problems.data(), pb);
     memcpy(b.h_work, plan.work.data(), wb);
     cudaError_t e = cudaMemcpyAsync(b.d_problems.ptr, b.h_problems, pb, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.d_work.ptr, b.h_work, wb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && eager) e = cudaEventRecord(b.staged_ev, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.d_counters.ptr, 0, (size_t)phases * sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(c, e, "batch plan upload");
     const int bucket = batch_bucket(plan.max_s);
@@ -371,6 +391,8 @@ int pmsp_densify_batch(pmsp_ctx* c, const pmsp_batch_item* items, int n, uint32_
         std::vector<uint8_t> sig = batch_signature(items, n, t);
         if (b.exec && sig == b.signature) {
             cudaError_t e = cudaGraphLaunch(b.exec, c->stream);
+            if (e == cudaSuccess && !b.staged_ev) e = cudaEventCreateWithFlags(&b.staged_ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(b.staged_ev, c->stream);  // the replay read the pinned copies
             return e == cudaSuccess ? PMSP_OK : cuda_fail(c, e, "graph launch");
         }
         drop_graph(b);
