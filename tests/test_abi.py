@@ -86,3 +86,52 @@ def test_create_without_a_gpu_reports_a_cuda_error(lib):
     h = ctypes.c_void_p(1)
     assert lib._lib.pmsp_create(ctypes.byref(h), None) == lib.PMSP_ECUDA
     assert h.value is None
+
+
+STRUCTS = ("pmsp_image", "pmsp_pose", "pmsp_params", "pmsp_maps", "pmsp_ctx_opts", "pmsp_batch_item",
+           "pmsp_tuning", "pmsp_request", "pmsp_serving_stats")
+
+
+def test_binding_structs_match_the_header_layout(lib, tmp_path):
+    """Every struct the binding marshals has the size and field offsets the C compiler
+    gives the header's declaration (a field added, dropped or reordered on one side
+    would pass garbage across the boundary)."""
+    import subprocess
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pmsp.h"', 'int main(void) {']
+    for s in STRUCTS:
+        lines.append(f'    printf("{s} size %zu\\n", sizeof({s}));')
+        for name, _ in getattr(lib, s)._fields_:
+            lines.append(f'    printf("{s} {name} %zu\\n", offsetof({s}, {name}));')
+    lines += ['    return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        s, name, value = line.split()
+        got[(s, name)] = int(value)
+    for s in STRUCTS:
+        cls = getattr(lib, s)
+        assert got[(s, "size")] == ctypes.sizeof(cls), s
+        for name, _ in cls._fields_:
+            assert got[(s, name)] == getattr(cls, name).offset, (s, name)
+
+
+def test_binding_constants_match_the_header(lib, tmp_path):
+    """Status codes, formats, memory kinds, flags and limits have the header's values."""
+    import subprocess
+    names = {n: n for n in ("PMSP_OK", "PMSP_EINVAL", "PMSP_ENOMEM", "PMSP_EADMIT", "PMSP_EBUSY", "PMSP_ETIMEDOUT",
+                            "PMSP_ECUDA", "PMSP_EDEVICE", "PMSP_ENOTFOUND", "PMSP_U8", "PMSP_F16", "PMSP_F32",
+                            "PMSP_HOST", "PMSP_DEVICE", "PMSP_BATCH_GRAPH", "PMSP_NOALLOC_MAX_ITEMS")}
+    names["MAX_SOURCES"] = "PMSP_MAX_SOURCES"
+    lines = ['#include <stdio.h>', '#include "pmsp.h"', 'int main(void) {']
+    lines += [f'    printf("{py} %lld\\n", (long long)({c}));' for py, c in names.items()]
+    lines += ['    return 0;', '}']
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        py, value = line.split()
+        assert getattr(lib, py) == int(value), py
