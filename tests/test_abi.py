@@ -135,3 +135,30 @@ def test_binding_constants_match_the_header(lib, tmp_path):
     for line in subprocess.check_output([str(exe)], text=True).splitlines():
         py, value = line.split()
         assert getattr(lib, py) == int(value), py
+
+
+def _prototypes():
+    """name -> list of parameter declarations, from the header's prototypes."""
+    src = open(os.path.join(ROOT, "include", "pmsp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pmsp_\w+)\s*\(([^;]*?)\)\s*;", src, flags=re.M | re.S):
+        params = " ".join(m.group(2).split())
+        out[m.group(1)] = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+    return out
+
+
+def test_binding_argument_lists_match_the_prototypes(lib):
+    """Each call's binding passes as many arguments as the header's prototype declares,
+    pointers where it declares pointers and numbers where it declares numbers."""
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+    so = lib._lib
+    for name, params in protos.items():
+        fn = getattr(so, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == len(params), name
+        for decl, t in zip(params, fn.argtypes):
+            is_ptr = "*" in decl
+            t_is_ptr = t is ctypes.c_void_p or t is ctypes.c_char_p or hasattr(t, "_type_") and \
+                isinstance(t, type) and issubclass(t, ctypes._Pointer)
+            assert is_ptr == t_is_ptr, (name, decl, t)
