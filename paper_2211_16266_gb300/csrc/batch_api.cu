@@ -391,8 +391,14 @@ int pmsp_densify_batch(pmsp_ctx* c, const pmsp_batch_item* items, int n, uint32_
         std::vector<uint8_t> sig = batch_signature(items, n, t);
         if (b.exec && sig == b.signature) {
             cudaError_t e = cudaGraphLaunch(b.exec, c->stream);
-            if (e == cudaSuccess && !b.staged_ev) e = cudaEventCreateWithFlags(&b.staged_ev, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventRecord(b.staged_ev, c->stream);  // the replay read the pinned copies
+            // the replay reads the pinned copies: mark it, unless the caller is recording
+            // the stream (an event recorded there could not be waited on afterwards)
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if (e == cudaSuccess && cudaStreamIsCapturing(c->stream, &cap) == cudaSuccess &&
+                cap == cudaStreamCaptureStatusNone) {
+                if (!b.staged_ev) e = cudaEventCreateWithFlags(&b.staged_ev, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventRecord(b.staged_ev, c->stream);
+            }
             return e == cudaSuccess ? PMSP_OK : cuda_fail(c, e, "graph launch");
         }
         drop_graph(b);
