@@ -357,6 +357,10 @@ typedef struct {
  * Densify n keyframes. tuning may be NULL (defaults). Returns PMSP_EINVAL if
  * any item is invalid (nothing is run). Device-memory batches return once
  * enqueued; a batch with host memory returns with the results on the host.
+ * The plan of a strategy-0 batch is staged through pinned host buffers that
+ * the context reuses: a call made while the previous call's upload (or graph
+ * replay) is still queued waits on the host until that has run. The first
+ * capture of a PMSP_BATCH_GRAPH batch waits for the context stream to idle.
  */
 int pmsp_densify_batch(pmsp_ctx* ctx, const pmsp_batch_item* items, int n, uint32_t flags,
                        const pmsp_tuning* tuning);
