@@ -162,3 +162,14 @@ def test_binding_argument_lists_match_the_prototypes(lib):
             t_is_ptr = t is ctypes.c_void_p or t is ctypes.c_char_p or hasattr(t, "_type_") and \
                 isinstance(t, type) and issubclass(t, ctypes._Pointer)
             assert is_ptr == t_is_ptr, (name, decl, t)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c", "c11"), ("c++", "c++11"), ("c++", "c++17")])
+def test_header_compiles_standalone(tmp_path, lang, std):
+    """include/pmsp.h compiles on its own, warning-free, as C and as C++ (extern "C")."""
+    import subprocess
+    src = tmp_path / ("t.c" if lang == "c" else "t.cpp")
+    src.write_text('#include "pmsp.h"\nint pmsp_header_check(void) { return PMSP_ABI_VERSION; }\n')
+    cc = "gcc" if lang == "c" else "g++"
+    subprocess.check_call([cc, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                           "-I", os.path.join(ROOT, "include"), str(src)])
