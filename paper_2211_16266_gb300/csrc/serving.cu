@@ -518,9 +518,10 @@ int pmsp_submit(pmsp_ctx* c, const pmsp_request* q, uint64_t* ticket) {
     r->bytes = (size_t)r->W * r->H * 6 * sizeof(float);
     r->tiles = (size_t)((r->W + TILE_W - 1) / TILE_W) * ((r->H + TILE_H - 1) / TILE_H);
     if (r->bytes > c->mem_cap) {
+        const size_t need = r->bytes;
         delete r;
         s.stats.rejected++;
-        return ctx_fail(c, PMSP_EADMIT, "request needs %zu bytes, above the cap", (size_t)r->W * r->H * 24);
+        return ctx_fail(c, PMSP_EADMIT, "request needs %zu bytes, above the cap", need);
     }
     for (int f : r->srcs) s.ring[f].pins++;
     for (int f : r->filters) s.ring[f].pins++;
