@@ -8,7 +8,6 @@ planes' costs differ by less than the FP32 rounding of the cost, the CUDA path
 and the oracle may keep different ones, which is why whole runs are compared
 by fraction.
 """
-import math
 
 import numpy as np
 import pytest

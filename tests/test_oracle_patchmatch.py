@@ -18,7 +18,6 @@ the cost it minimises is pinned in test_oracle_cost.py. Here:
 * the state never leaves the search space (ranges in [d_min, d_max], unit
   normals facing the camera) even when the true surface lies outside it.
 """
-import math
 
 import numpy as np
 import pytest

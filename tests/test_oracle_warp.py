@@ -18,7 +18,6 @@ random initialisation. Pins:
 import math
 
 import numpy as np
-import pytest
 
 import oracle
 import scenes
