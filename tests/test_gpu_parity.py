@@ -279,6 +279,49 @@ def test_invalid_arguments_are_rejected(pm, ctx):
     pm.pmsp_sync(ctx)
 
 
+def test_misaligned_device_images_are_refused(pm, ctx):
+    """Device images are read in place element by element: an f16 or f32
+    device image whose pointer or pitch is not a multiple of the element size
+    is refused with PMSP_EINVAL before anything is launched, as a reference
+    and as a source, by the single and the no-allocation entry points."""
+    import ctypes
+    import torch
+    prob = _problem("c0")
+    H, W = prob.ref.image.shape
+    buf = torch.zeros(H * (4 * W + 8) + 16, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr()
+    bad = [pm.pmsp_image(W, H, 2 * W + 1, pm.PMSP_F16, pm.PMSP_DEVICE, base),
+           pm.pmsp_image(W, H, 2 * W + 2, pm.PMSP_F16, pm.PMSP_DEVICE, base + 1),
+           pm.pmsp_image(W, H, 4 * W + 2, pm.PMSP_F32, pm.PMSP_DEVICE, base),
+           pm.pmsp_image(W, H, 4 * W + 4, pm.PMSP_F32, pm.PMSP_DEVICE, base + 2)]
+    keep = []
+    ref = pm.make_image(_dev(prob.ref.image), keep)
+    good = [pm.make_image(_dev(f.image), keep) for f in prob.srcs]
+    rp = pm.make_pose((prob.ref.R, prob.ref.t))
+    poses = (pm.pmsp_pose * 2)(*[pm.make_pose((f.R, f.t)) for f in prob.srcs])
+    params = pm.make_params(prob.params)
+    out = pm.Maps.empty(W, H, device="cuda")
+    m = out.c()
+    for b in bad:
+        srcs = (pm.pmsp_image * 2)(*good)
+        rc = pm._lib.pmsp_densify(ctx.h, ctypes.byref(b), ctypes.byref(rp), srcs, poses, 2,
+                                  ctypes.byref(params), ctypes.byref(m))
+        assert rc == pm.PMSP_EINVAL, rc
+        srcs = (pm.pmsp_image * 2)(good[0], b)
+        rc = pm._lib.pmsp_densify(ctx.h, ctypes.byref(ref), ctypes.byref(rp), srcs, poses, 2,
+                                  ctypes.byref(params), ctypes.byref(m))
+        assert rc == pm.PMSP_EINVAL, rc
+        item = pm.pmsp_batch_item(ref, rp, srcs, poses, 2, params, m)
+        rc = pm._lib.pmsp_densify_batch_noalloc(ctx.h, ctypes.byref(item), 1)
+        assert rc == pm.PMSP_EINVAL, rc
+    # the context stays usable, and aligned f16 device images still run
+    pm.pmsp_densify(ctx, *_gpu_args(prob), dict(prob.params, iterations=1))
+    f16 = [_dev((f.image / 255.0).astype(np.float16)) for f in prob.srcs]
+    pm.pmsp_densify(ctx, _dev(prob.ref.image), (prob.ref.R, prob.ref.t), f16,
+                    [(f.R, f.t) for f in prob.srcs], dict(prob.params, iterations=1))
+    pm.pmsp_sync(ctx)
+
+
 # ---------------------------------------------- full size, sampled parity
 
 def test_full_size_sampled_parity(pm, ctx):
@@ -312,16 +355,27 @@ def test_full_size_sampled_parity(pm, ctx):
     assert np.mean(ok_c) >= 0.995 and np.mean(ok_d) >= 0.995
 
 
-# At 3840x1920 an FP32 sample position carries about 1e-4 px of error (1e-7 rad
-# from the FP32 bearings, rotation and arctangent, at 611 px per radian). On the
-# sigma = 2 DN noise of this workload, pixels still holding poor hypotheses after
-# 8 iterations (costs 0.45-0.7; only 36 % of pixels are within 5 % of the true
-# range at this size) sample patches of noise, where that error moves the NCC by
-# up to ~1e-4: measured, 99.0-99.5 % of sampled stored costs are within 1e-4 of
-# the oracle, against 99.93 % at 1920x960 with the same noise and 100 % at
-# 3840x1920 without it. The stored-cost bar here is therefore 98.5 %; the range
-# bar stays 99.5 %.
-COST_FRACTION_4K_NOISE = 0.985
+
+
+def test_full_size_whole_run_parity(pm, ctx):
+    """1920x960, 6 sources, 11x11/2, 8 iterations, best-3 (the benchmarked
+    keyframe): the whole GPU run against the whole FP64 oracle run, every
+    pixel, at the densification's bar (cost 1e-4, range 0.5 %, on 99.5 % of
+    pixels), with the ground-truth accuracy of both sides."""
+    prob = scenes.config1()
+    m = pm.pmsp_densify(ctx, *_gpu_args(prob), prob.params)
+    gd, gc = (a.cpu().numpy().astype(np.float64) for a in (m.depth, m.cost))
+    od, on, oc = oracle.Problem.from_scene(prob).densify()
+    depth_ok = np.abs(gd - od) / od <= DEPTH_TOL
+    cost_ok = np.abs(gc - oc) <= COST_TOL
+    gt = prob.ref.range
+    gt_gpu = np.mean(np.abs(gd - gt) / gt < 0.05)
+    gt_orc = np.mean(np.abs(od - gt) / gt < 0.05)
+    print(f"1920x960 whole run: depth parity {depth_ok.mean():.5f} cost parity {cost_ok.mean():.5f} "
+          f"GT<5%: gpu {gt_gpu:.4f} oracle {gt_orc:.4f}")
+    assert depth_ok.mean() >= 0.995
+    assert cost_ok.mean() >= 0.995
+    assert abs(gt_gpu - gt_orc) < 0.005
 
 
 @pytest.mark.parametrize("fmt", ["f16", "u8"])
@@ -342,7 +396,7 @@ def test_full_size_precision_forms_sampled_parity(pm, ctx, fmt):
     gt = prob.ref.range
     print(f"3840x1920 {fmt}: stored costs within 1e-4 {np.mean(errs <= COST_TOL):.4f}, "
           f"GT within 5% {np.mean(np.abs(d - gt) / gt < 0.05):.4f}")
-    assert np.mean(errs <= COST_TOL) >= COST_FRACTION_4K_NOISE
+    assert np.mean(errs <= COST_TOL) >= 0.995
     state = _maps_from(pm, d, n, c)
     pm.pmsp_halfsweep(ctx, *args, prob.params, 1, 8, state)
     gd, gc = state.depth.cpu().numpy(), state.cost.cpu().numpy()
@@ -355,7 +409,7 @@ def test_full_size_precision_forms_sampled_parity(pm, ctx, fmt):
         ok_c.append(abs(oc - gc[v, u]) <= COST_TOL)
         ok_d.append(abs(od - gd[v, u]) / od <= DEPTH_TOL)
     print(f"3840x1920 {fmt}: one more half-sweep, costs {np.mean(ok_c):.4f}, ranges {np.mean(ok_d):.4f}")
-    assert np.mean(ok_c) >= COST_FRACTION_4K_NOISE and np.mean(ok_d) >= 0.995
+    assert np.mean(ok_c) >= 0.995 and np.mean(ok_d) >= 0.995
 
 
 # ------------------------------------------------------------ projection
