@@ -76,7 +76,10 @@ typedef enum { PMSP_U8 = 0, PMSP_F16 = 1, PMSP_F32 = 2 } pmsp_format;
 typedef enum { PMSP_HOST = 0, PMSP_DEVICE = 1 } pmsp_memory;
 
 /* A grayscale panorama. pitch_bytes >= w * element size; data is host or
- * device memory according to `memory`. */
+ * device memory according to `memory`. Device images are read in place by
+ * element, so their data pointer and pitch_bytes must both be multiples of
+ * the element size (2 bytes for F16, 4 for F32); any other device image is
+ * refused with PMSP_EINVAL before a launch. Host images may have any pitch. */
 typedef struct {
     int32_t w, h;
     int64_t pitch_bytes;

@@ -166,6 +166,7 @@ static_assert((NA_OFF_LINEAR - NA_OFF_PREFIX) % 4 == 0, "tile offsets are stored
 
 std::mutex g_setup_mu;
 void* g_scratch_addr[128];  // device address of the scratch array, per device ordinal
+int g_resident[128];        // SMs x resident blocks of noalloc_kernel, per device ordinal
 bool g_scratch_ready[128];
 
 }  // namespace
@@ -184,18 +185,29 @@ extern "C" int pmsp_densify_batch_noalloc(pmsp_ctx* c, const pmsp_batch_item* it
     if (c->device < 0 || c->device >= 128) return ctx_fail(c, PMSP_EINVAL, "device ordinal %d out of range", c->device);
 
     // set-up, once per device, with that device current: the device address of
-    // the scratch array (its host-side name is only a stand-in)
+    // the scratch array (its host-side name is only a stand-in) and the number
+    // of blocks the persistent kernel keeps resident
     void* scratch = nullptr;
+    int resident = 0;
     {
         std::lock_guard<std::mutex> lk(g_setup_mu);
         if (!g_scratch_ready[c->device]) {
             void* p = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) return cuda_fail(c, e, "scratch address lookup");
+            int sms = 0, occ = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+            if (e != cudaSuccess) return cuda_fail(c, e, "SM count query");
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, noalloc_kernel, BLOCK_THREADS, 0);
+            if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
+            if (sms < 1 || occ < 1)
+                return ctx_fail(c, PMSP_ECUDA, "no-allocation kernel cannot run: %d SMs x %d blocks", sms, occ);
             g_scratch_addr[c->device] = p;
+            g_resident[c->device] = sms * occ;
             g_scratch_ready[c->device] = true;
         }
         scratch = g_scratch_addr[c->device];
+        resident = g_resident[c->device];
     }
 
     // host image of the used part of the scratch, on the stack (no allocation)
@@ -269,11 +281,7 @@ extern "C" int pmsp_densify_batch_noalloc(pmsp_ctx* c, const pmsp_batch_item* it
     if (e == cudaSuccess) e = store(NA_OFF_LINEAR, (size_t)n * PMSP_MAX_SOURCES * sizeof(LinearSrc));
     if (e == cudaSuccess) e = store(NA_OFF_PARAMS, (size_t)n * sizeof(PixelParams));
     if (e != cudaSuccess) return cuda_fail(c, e, "no-allocation descriptor upload");
-    int sms = 0, occ = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, noalloc_kernel, BLOCK_THREADS, 0) != cudaSuccess || occ < 1)
-        occ = 1;
-    const int grid = std::max(1, std::min(total, sms * occ));
+    const int grid = std::max(1, std::min(total, resident));
     for (int ph = 0; ph < max_phases; ++ph) {
         noalloc_kernel<<<grid, BLOCK_THREADS, 0, c->stream>>>(static_cast<unsigned char*>(scratch), ph, n);
         e = cudaGetLastError();

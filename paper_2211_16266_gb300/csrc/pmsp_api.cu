@@ -76,6 +76,10 @@ int check_image(pmsp_ctx* c, const pmsp_image* im, const char* what) {
         return ctx_fail(c, PMSP_EINVAL, "%s: pitch %lld < row bytes", what, (long long)im->pitch_bytes);
     if (im->memory != PMSP_HOST && im->memory != PMSP_DEVICE)
         return ctx_fail(c, PMSP_EINVAL, "%s: unknown memory kind", what);
+    // device images are read in place element by element (the reference tile,
+    // the no-alloc source fetch): a misaligned row would fault on the GPU
+    if (im->memory == PMSP_DEVICE && (((uintptr_t)im->data % eb) != 0 || (im->pitch_bytes % (int64_t)eb) != 0))
+        return ctx_fail(c, PMSP_EINVAL, "%s: device data and pitch must be multiples of %zu bytes", what, eb);
     return PMSP_OK;
 }
 

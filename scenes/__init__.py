@@ -286,7 +286,8 @@ def trajectory_problem(W, H, n_src, seed_scene=1001, seed_traj=2000, n_objects=2
         img, rg = scene.render(R, t, W, H, with_range=with_range)
         if noise_sigma > 0:
             img = img + nrng.normal(0.0, noise_sigma, size=img.shape)
-        im = quantise_u8(img) if fmt == "u8" else (np.clip(img, 0, 255) / 255.0).astype(np.float16)
+        im = quantise_u8(img) if fmt == "u8" else \
+            (np.clip(img, 0, 255) / 255.0).astype(np.float16 if fmt == "f16" else np.float32)
         frames.append(Frame(R, t, C, im, rg))
     mid = n_src // 2
     ref = frames[mid]

@@ -36,7 +36,9 @@ def test_noalloc_matches_batched_entry_point_twice():
                      sigma_space=4.0, n_refine=6, neighbor_table=1, seed=5, keyframe_id=77)
     p3 = scenes.trajectory_problem(256, 128, 4, seed_scene=1012, fmt="f16")
     p3.params = dict(p1.params, iterations=4, keyframe_id=9)
-    probs = [p1, p2, p3]
+    p4 = scenes.trajectory_problem(192, 96, 3, seed_scene=1014, fmt="f32")
+    p4.params = dict(p1.params, iterations=3, best_k=2, keyframe_id=4)
+    probs = [p1, p2, p3, p4]
     args = [(_dev(p.ref.image), (p.ref.R, p.ref.t), [_dev(f.image) for f in p.srcs], [(f.R, f.t) for f in p.srcs])
             for p in probs]
     with pm.Context(0) as ctx:
