@@ -12,8 +12,10 @@ the cost it minimises is pinned in test_oracle_cost.py. Here:
 * the random initial planes and the refinement proposals come from Philox
   blocks laid out as (pixel, iteration, stage, 0) under key (seed, keyframe
   id), one uniform per perturbed component, checked with numpy's Philox;
-* brute force: an exhaustive plane sweep on a tiny panorama does not beat the
-  PatchMatch result by more than a small margin on almost all pixels;
+* brute force: an exhaustive plane sweep (256 inverse-range levels x 162
+  normals) on a tiny panorama does not beat the PatchMatch result by more than
+  1e-3 on 95 % of pixels, and the final range is the sweep's optimum along the
+  final normal within one level;
 * on the rendered 256x128 room the result matches ground-truth range;
 * the state never leaves the search space (ranges in [d_min, d_max], unit
   normals facing the camera) even when the true surface lies outside it.
@@ -175,27 +177,6 @@ def _icosphere(level):
     return np.array(V)
 
 
-def test_patchmatch_reaches_exhaustive_sweep_minimum():
-    """48x24 panorama, one source 0.2 m to the side: brute force over 64
-    inverse-range levels x 162 icosphere normals vs 16 PatchMatch iterations."""
-    W, H = 48, 24
-    scene = scenes.Scene(seed=1234)
-    C = np.array([0.2, 0.1, -0.3])
-    R0, t0 = scenes.pose_from_centre(scenes.rot_y(0.3), C)
-    R1, t1 = scenes.pose_from_centre(scenes.rot_y(0.3), C + np.array([0.2, 0.0, 0.0]))
-    img0, _ = scene.render(R0, t0, W, H)
-    img1, _ = scene.render(R1, t1, W, H)
-    pb = oracle.Problem(img0 / 255.0, (R0, t0), [img1 / 255.0], [(R1, t1)], patch_w=7,
-                        patch_stride=1, iterations=16, best_k=1)
-    N = _icosphere(2)
-    assert len(N) == 162
-    sweep_cost, _ = pb.plane_sweep(64, N)
-    _, _, c = pb.densify()
-    assert np.mean(c <= sweep_cost + 1e-3) > 0.75
-    assert np.mean(c <= sweep_cost + 5e-3) > 0.95
-    assert np.median(c) <= np.median(sweep_cost) + 1e-3
-
-
 def test_config0_matches_ground_truth():
     prob = scenes.config0()
     pb = oracle.Problem.from_scene(prob)
@@ -280,3 +261,88 @@ def test_refinement_draw_layout():
         assert np.allclose(n[:, v, u], m, atol=1e-12, rtol=0)
         assert c[v, u] <= 2.0
     assert np.array_equal(d[other], d0[other])
+
+
+def test_refinement_schedule_shrinks_around_current_best():
+    """The six refinement tests of Sec. III-C, seen one at a time through
+    n_refine = 1..6 from the same state (incumbent cost above any cost, every
+    neighbour facing away): result m equals result m - 1 or has a strictly lower
+    cost; an accepted test m moves the inverse range at most s_m (1/d_min -
+    1/d_max) from result m - 1 (the current best, not the half-sweep's starting
+    plane), s_m = 2^-m, and over many pixels the moves fill that bound (each
+    test draws its own uniform), so the search range halves at every test."""
+    W, H, seed, kf, it, colour = 64, 32, 21, 6, 3, 0
+    scene = scenes.Scene(seed=1234)
+    C = np.array([0.2, 0.1, -0.3])
+    R0, t0 = scenes.pose_from_centre(scenes.rot_y(0.3), C)
+    R1, t1 = scenes.pose_from_centre(scenes.rot_y(0.3), C + np.array([0.2, 0.0, 0.0]))
+    img0, _ = scene.render(R0, t0, W, H)
+    img1, _ = scene.render(R1, t1, W, H)
+    d_min, d_max = 0.3, 10.0
+    span = 1 / d_min - 1 / d_max
+    r = np.stack([oracle.bearing(W, H, u, v) for v in range(H) for u in range(W)], 1).reshape(3, H, W)
+    rng = np.random.default_rng(2)
+    d0 = rng.uniform(0.5, 5.0, (H, W))
+    n0 = -r + 0.3 * rng.normal(size=(3, H, W))
+    n0 /= np.linalg.norm(n0, axis=0)
+    n0 = np.where(np.sum(n0 * r, 0) < 0, n0, -n0)
+    act = ((np.arange(W)[None, :] + np.arange(H)[:, None]) % 2) == colour
+    n0[:, ~act] = r[:, ~act]
+    chain = [(d0, np.full((H, W), 5.0))]
+    for m in range(1, 7):
+        pb = oracle.Problem(img0 / 255.0, (R0, t0), [img1 / 255.0], [(R1, t1)], d_min=d_min, d_max=d_max,
+                            patch_w=5, patch_stride=1, iterations=1, best_k=1, n_refine=m, seed=seed,
+                            keyframe_id=kf)
+        d, n, c = d0.copy(), np.ascontiguousarray(n0).copy(), np.full((H, W), 5.0)
+        pb.halfsweep(d, n, c, colour, it)
+        chain.append((d, c))
+    for m in range(1, 7):
+        (dp, cp), (dm, cm) = chain[m - 1], chain[m]
+        moved = act & (dm != dp)
+        assert np.all(cm[act] <= cp[act])
+        assert np.all(cm[moved] < cp[moved])
+        step = np.abs(1 / dm - 1 / dp)[moved] / (2.0 ** -m * span)
+        assert np.all(step <= 1 + 1e-9), (m, step.max())
+        assert moved.sum() >= 40, (m, moved.sum())
+        assert step.max() >= 0.8, (m, step.max())
+
+
+def test_patchmatch_reaches_exhaustive_sweep_minimum():
+    """Brute force on a tiny input: a 32x16 panorama, one source 0.2 m to the
+    side, 7x7 window. (1) An exhaustive sweep over 256 inverse-range levels x
+    162 icosphere normals (level 2) does not beat the PatchMatch cost after
+    128 iterations by more than 1e-3 on 95 % of pixels. (2) The final plane
+    is a depth optimum along its own normal: a sweep of the same 256 levels
+    with that normal finds its minimum within one level of the PatchMatch
+    range on 98 % of pixels and no cost below it by more than 1e-3 on 99 %.
+    Part (2) states the depth check on the PatchMatch plane's own normal
+    because the continuous normals beat the 162 sampled ones on almost every
+    pixel, so the 2-D sweep's argmin range carries the normal sampling's bias.
+    (Measured on the oracle: 97.3 %, 99.2 %, 100 %; with 16 iterations 67 %
+    and 80 %: the pin needs a search that converges.)"""
+    W, H = 32, 16
+    scene = scenes.Scene(seed=1234)
+    C = np.array([0.2, 0.1, -0.3])
+    R0, t0 = scenes.pose_from_centre(scenes.rot_y(0.3), C)
+    R1, t1 = scenes.pose_from_centre(scenes.rot_y(0.3), C + np.array([0.2, 0.0, 0.0]))
+    img0, _ = scene.render(R0, t0, W, H)
+    img1, _ = scene.render(R1, t1, W, H)
+    pb = oracle.Problem(img0 / 255.0, (R0, t0), [img1 / 255.0], [(R1, t1)], patch_w=7,
+                        patch_stride=1, iterations=128, best_k=1)
+    N = _icosphere(2)
+    assert len(N) == 162
+    L = 256
+    sweep_cost, _ = pb.plane_sweep(L, N)
+    d, n, c = pb.densify()
+    assert np.mean(c <= sweep_cost + 1e-3) >= 0.95
+    inv = 1.0 / 10.0 + (1.0 / 0.3 - 1.0 / 10.0) * np.arange(L) / (L - 1)
+    level = np.zeros((H, W))
+    gap = np.zeros((H, W))
+    for v in range(H):
+        for u in range(W):
+            line = np.array([pb.cost(u, v, 1.0 / x, n[:, v, u]) for x in inv])
+            k = int(np.argmin(line))
+            level[v, u] = abs(1.0 / d[v, u] - inv[k]) / (inv[1] - inv[0])
+            gap[v, u] = c[v, u] - line[k]
+    assert np.mean(level <= 1.0) >= 0.98
+    assert np.mean(gap <= 1e-3) >= 0.99

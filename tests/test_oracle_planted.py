@@ -107,6 +107,16 @@ PLANTED = [
     ("refine_range_not_halved", "double s = ldexp(1.0, -(k + 1));", "double s = 1.0;", PM),
     ("refine_one_sided_depth", "double inv = 1.0 / bd + (2.0 * r[0] - 1.0) * s * (inv_hi - inv_lo);",
      "double inv = 1.0 / bd + r[0] * s * (inv_hi - inv_lo);", PM),
+    # caught only by the refinement-schedule pin (tests after the first)
+    ("refine_scale_quartered", "double s = ldexp(1.0, -(k + 1));", "double s = ldexp(1.0, -(2 * k + 1));", PM),
+    ("refine_range_around_starting_plane", "double inv = 1.0 / bd + (2.0 * r[0] - 1.0)",
+     "double inv = 1.0 / depth[i] + (2.0 * r[0] - 1.0)", PM),
+    # caught only by the brute-force sweep pin (slower convergence, every step well formed)
+    ("refine_normal_around_starting_plane",
+     "double nc[3] = {bn[0] + s * (2.0 * r[1] - 1.0), bn[1] + s * (2.0 * r[2] - 1.0),\n"
+     "                        bn[2] + s * (2.0 * r[3] - 1.0)};",
+     "double nc[3] = {normal[i] + s * (2.0 * r[1] - 1.0), normal[N + i] + s * (2.0 * r[2] - 1.0),\n"
+     "                        normal[2 * N + i] + s * (2.0 * r[3] - 1.0)};", PM),
     # consistency filter (Sec. III)
     ("filter_seam_not_wrapped", "du -= W * floor(du / W + 0.5);", "du -= 0.0;", FILTER),
     ("filter_min_views_strict", "out[i] = (d > 0 && cnt >= min_views) ? d : 0.0;",
