@@ -322,6 +322,35 @@ int pmsp_sample_bilinear(pmsp_ctx* ctx, const pmsp_image* img, int n, const floa
 int pmsp_project(pmsp_ctx* ctx, int W, int H, int n, const float* dirs, float* uc, float* vc,
                  int memory);
 
+/*
+ * Measured peaks of the units the cost kernel is bound by (its roofline; the
+ * paper reports no per-unit figures). The cost of one view-sample is plain FP32
+ * arithmetic, special-function square roots and reciprocals and one texture
+ * gather, so the denominators are these rates, each from a self-terminating
+ * probe over every SM (fixed loop counts, independent chains), timed with CUDA
+ * events on the context's stream, best of three:
+ *   fp32_fma_per_s    scalar FMAs per second, all FP32 lanes
+ *   fp32x2_fma_per_s  FMAs per second issued as packed f32x2 instructions
+ *   sfu_per_s         rsqrt.approx results per second
+ *   gather_l1_per_s   tex2Dgather results per second from an L1-resident texture
+ *   gather_l2_per_s   the same at scattered texels of a 16 MB (L2-resident) texture
+ *   sm_clock_mhz_max  the device's maximum SM clock (the probes run at the live clock)
+ * Allocates a few MB for the probes and frees them; synchronous; about 0.2 s.
+ * Errors: PMSP_EINVAL for NULL arguments, PMSP_ECUDA / PMSP_ENOMEM from CUDA.
+ */
+typedef struct {
+    double fp32_fma_per_s;
+    double fp32x2_fma_per_s;
+    double sfu_per_s;
+    double gather_l1_per_s;
+    double gather_l2_per_s;
+    double sm_clock_mhz_max;
+    int32_t sms;
+    int32_t reserved;
+} pmsp_peaks;
+
+int pmsp_measure_peaks(pmsp_ctx* ctx, pmsp_peaks* out);
+
 /* ------------------------------------------------------------------------
  * Batched densification: many keyframes of different sizes and view counts
  * in one pass. Every phase (initialisation colours, then each half-sweep) is

@@ -112,11 +112,19 @@ class pmsp_tuning(ctypes.Structure):
                 ("strategy", ctypes.c_int32), ("tile", ctypes.c_int32)]
 
 
+class pmsp_peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp32x2_fma_per_s", ctypes.c_double),
+                ("sfu_per_s", ctypes.c_double), ("gather_l1_per_s", ctypes.c_double),
+                ("gather_l2_per_s", ctypes.c_double), ("sm_clock_mhz_max", ctypes.c_double),
+                ("sms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 PMSP_BATCH_GRAPH = 1
 _SIGS["pmsp_densify_batch"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int, ctypes.c_uint32,
                                 ctypes.POINTER(pmsp_tuning)], ctypes.c_int)
 _SIGS["pmsp_autotune"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int, ctypes.c_float,
                            ctypes.POINTER(pmsp_tuning)], ctypes.c_int)
+_SIGS["pmsp_measure_peaks"] = ([_P, ctypes.POINTER(pmsp_peaks)], ctypes.c_int)
 _SIGS["pmsp_densify_batch_noalloc"] = ([_P, ctypes.POINTER(pmsp_batch_item), ctypes.c_int], ctypes.c_int)
 PMSP_NOALLOC_MAX_ITEMS = 16
 _SIGS["pmsp_warp_init"] = ([_P, _I, _O, _I, _O, ctypes.c_int, _R, _M, _O, _M, _F], ctypes.c_int)
@@ -488,6 +496,13 @@ def pmsp_sample_bilinear(ctx, img, uc, vc):
         out = np.zeros_like(uc)
     ctx.check(_lib.pmsp_sample_bilinear(ctx.h, ctypes.byref(im), int(uc.shape[0]), _ptr(uc), _ptr(vc), _ptr(out)))
     return out
+
+
+def pmsp_measure_peaks(ctx):
+    """Measured FP32, special-function and gather rates of the device (dict)."""
+    out = pmsp_peaks()
+    ctx.check(_lib.pmsp_measure_peaks(ctx.h, ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in pmsp_peaks._fields_ if k != "reserved"}
 
 
 def pmsp_project(ctx, W, H, dirs):

@@ -89,7 +89,7 @@ def test_create_without_a_gpu_reports_a_cuda_error(lib):
 
 
 STRUCTS = ("pmsp_image", "pmsp_pose", "pmsp_params", "pmsp_maps", "pmsp_ctx_opts", "pmsp_batch_item",
-           "pmsp_tuning", "pmsp_request", "pmsp_serving_stats")
+           "pmsp_tuning", "pmsp_request", "pmsp_serving_stats", "pmsp_peaks")
 
 
 def test_binding_structs_match_the_header_layout(lib, tmp_path):
