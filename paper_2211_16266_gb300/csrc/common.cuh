@@ -69,8 +69,9 @@ struct alignas(16) PixelParams {
     unsigned* err;
     // Constants of views (2p, 2p + 1) interleaved, so one packed FP32
     // instruction reads the same constant of both views (an odd last view is
-    // paired with itself).
-    struct ViewPair {
+    // paired with itself). 16-byte aligned: the batched kernel reads a pair
+    // from shared memory as 16-byte words.
+    struct alignas(16) ViewPair {
         float2 R[9];
         float2 t[3];
         float2 su, nsv;    // nsv = -sv: the paired projection computes -lat

@@ -256,6 +256,73 @@ struct SharedViews {
     }
 };
 
+// The constants of a view pair the paired sample loop reads, and the texture
+// of a view. Kernel parameters (ParamViews): member reads at the point of use,
+// which become constant-bank operands. Shared memory (SharedViews, the batched
+// kernel): volatile 16-byte loads at every sample, so the compiler reloads
+// them instead of keeping every pair's constants in registers across the
+// sample loop.
+template <class VA>
+struct PairOf {  // kernel parameters: each constant read where it is used
+    const PixelParams::ViewPair& V;
+    __device__ __forceinline__ float2 r1() const { return V.R[1]; }
+    __device__ __forceinline__ float2 r4() const { return V.R[4]; }
+    __device__ __forceinline__ float2 r7() const { return V.R[7]; }
+    __device__ __forceinline__ float2 t0() const { return V.t[0]; }
+    __device__ __forceinline__ float2 t1() const { return V.t[1]; }
+    __device__ __forceinline__ float2 t2() const { return V.t[2]; }
+    __device__ __forceinline__ float2 su() const { return V.su; }
+    __device__ __forceinline__ float2 nsv() const { return V.nsv; }
+    __device__ __forceinline__ float2 inv_w() const { return V.inv_w; }
+    __device__ __forceinline__ float2 inv_h() const { return V.inv_h; }
+};
+
+template <>
+struct PairOf<SharedViews> {  // shared memory: the pair's words loaded once per use of the pair
+    float4 a, b, c, d, e, f, g;
+    __device__ __forceinline__ explicit PairOf(const PixelParams::ViewPair& V) {
+        // ViewPair as 8 16-byte words: (R0 R1) (R2 R3) (R4 R5) (R6 R7) (R8 t0) (t1 t2) (su nsv) (inv_w inv_h)
+        const float4* q = reinterpret_cast<const float4*>(&V);
+        a = SharedViews::ld4(q);
+        b = SharedViews::ld4(q + 2);
+        c = SharedViews::ld4(q + 3);
+        d = SharedViews::ld4(q + 4);
+        e = SharedViews::ld4(q + 5);
+        f = SharedViews::ld4(q + 6);
+        g = SharedViews::ld4(q + 7);
+    }
+    __device__ __forceinline__ float2 r1() const { return make_float2(a.z, a.w); }
+    __device__ __forceinline__ float2 r4() const { return make_float2(b.x, b.y); }
+    __device__ __forceinline__ float2 r7() const { return make_float2(c.z, c.w); }
+    __device__ __forceinline__ float2 t0() const { return make_float2(d.z, d.w); }
+    __device__ __forceinline__ float2 t1() const { return make_float2(e.x, e.y); }
+    __device__ __forceinline__ float2 t2() const { return make_float2(e.z, e.w); }
+    __device__ __forceinline__ float2 su() const { return make_float2(f.x, f.y); }
+    __device__ __forceinline__ float2 nsv() const { return make_float2(f.z, f.w); }
+    __device__ __forceinline__ float2 inv_w() const { return make_float2(g.x, g.y); }
+    __device__ __forceinline__ float2 inv_h() const { return make_float2(g.z, g.w); }
+};
+
+template <class VA>
+__device__ __forceinline__ PairOf<VA> pair_of(const PixelParams::ViewPair& V) {
+    if constexpr (std::is_same<VA, SharedViews>::value)
+        return PairOf<SharedViews>(V);
+    else
+        return PairOf<VA>{V};
+}
+
+template <class VA>
+__device__ __forceinline__ cudaTextureObject_t view_tex(const SourceView& V) {
+    if constexpr (std::is_same<VA, SharedViews>::value) {
+        unsigned long long t;
+        const unsigned a = (unsigned)__cvta_generic_to_shared(&V.tex);
+        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(t) : "r"(a));
+        return (cudaTextureObject_t)t;
+    } else {
+        return V.tex;
+    }
+}
+
 // Intensity of source view V at the projection of reference-frame point X.
 template <class VA>
 __device__ __forceinline__ float view_sample(const SourceView& V, float X, float Y, float Z) {
@@ -376,16 +443,16 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const SM& sm, 
 // sample_bilinear_half, operation for operation. Two phases: the source
 // coordinates of every pair first, then the gathers and interpolation, so the
 // gathers of all pairs are in flight together (2 % faster than pair by pair).
-template <int NP>
+template <int NP, class VA>
 __device__ __forceinline__ void pairs_sample(const PixelParams& P, float alpha, float beta, int cx, float2 (&J)[NP]) {
     float2 fx[NP], fy[NP], xn[NP], yn[NP];
     const float2 av = pair(alpha), bv = pair(beta);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        const PixelParams::ViewPair& VP = P.pairs[q];
-        const float2 Yx = fma2(av, g_colU[q][0][cx], fma2(bv, VP.R[1], VP.t[0]));
-        const float2 Yy = fma2(av, g_colU[q][1][cx], fma2(bv, VP.R[4], VP.t[1]));
-        const float2 Yz = fma2(av, g_colU[q][2][cx], fma2(bv, VP.R[7], VP.t[2]));
+        const auto VP = pair_of<VA>(P.pairs[q]);
+        const float2 Yx = fma2(av, g_colU[q][0][cx], fma2(bv, VP.r1(), VP.t0()));
+        const float2 Yy = fma2(av, g_colU[q][1][cx], fma2(bv, VP.r4(), VP.t1()));
+        const float2 Yz = fma2(av, g_colU[q][2][cx], fma2(bv, VP.r7(), VP.t2()));
         const float2 q2 = fma2(Yx, Yx, mul2(Yz, Yz));
         const float2 rho = make_float2(sqrt_approx(q2.x), sqrt_approx(q2.y));
         const float2 dl = add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y)));
@@ -398,18 +465,18 @@ __device__ __forceinline__ void pairs_sample(const PixelParams& P, float alpha, 
         atan2x_poly2_dual(mul2(ql, ql), mul2(qt, qt), pl, pt);
         const float2 al = mul2(ql, pl), nlat = mul2(qt, pt);
         const bool f0 = Yz.x >= 0.f, f1 = Yz.y >= 0.f;
-        const float2 qu = fma2(al, make_float2(f0 ? VP.su.x : -VP.su.x, f1 ? VP.su.y : -VP.su.y), pair(0.5f));
-        const float2 qv = fma2(nlat, VP.nsv, pair(0.5f));
+        const float2 qu = fma2(al, make_float2(f0 ? VP.su().x : -VP.su().x, f1 ? VP.su().y : -VP.su().y), pair(0.5f));
+        const float2 qv = fma2(nlat, VP.nsv(), pair(0.5f));
         const float2 fi = floor_small2(qu), fj = floor_small2(qv);
         fx[q] = add2(qu, make_float2(-fi.x, -fi.y));
         fy[q] = add2(qv, make_float2(-fj.x, -fj.y));
-        xn[q] = fma2(fi, VP.inv_w, make_float2(f0 ? 0.5f : 0.0f, f1 ? 0.5f : 0.0f));
-        yn[q] = fma2(fj, VP.inv_h, pair(0.5f));
+        xn[q] = fma2(fi, VP.inv_w(), make_float2(f0 ? 0.5f : 0.0f, f1 ? 0.5f : 0.0f));
+        yn[q] = fma2(fj, VP.inv_h(), pair(0.5f));
     }
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        const float4 g0 = tex2Dgather<float4>(P.src[2 * q].tex, xn[q].x, yn[q].x, 0);
-        const float4 g1 = tex2Dgather<float4>(P.src[2 * q + 1].tex, xn[q].y, yn[q].y, 0);
+        const float4 g0 = tex2Dgather<float4>(view_tex<VA>(P.src[2 * q]), xn[q].x, yn[q].x, 0);
+        const float4 g1 = tex2Dgather<float4>(view_tex<VA>(P.src[2 * q + 1]), xn[q].y, yn[q].y, 0);
         const float top0 = fmaf(fx[q].x, g0.z - g0.w, g0.w), bot0 = fmaf(fx[q].x, g0.y - g0.x, g0.x);
         const float top1 = fmaf(fx[q].y, g1.z - g1.w, g1.w), bot1 = fmaf(fx[q].y, g1.y - g1.x, g1.x);
         J[q] = make_float2(fmaf(fy[q].x, bot0 - top0, top0), fmaf(fy[q].y, bot1 - top1, top1));
@@ -418,7 +485,7 @@ __device__ __forceinline__ void pairs_sample(const PixelParams& P, float alpha, 
 
 // plane_cost for exactly NS >= 2 views held in kernel parameters, with the
 // views processed in pairs (packed FP32) and an odd last view on its own.
-template <int NS, int WIN, class SM>
+template <int NS, int WIN, class SM, class VA>
 __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const SM& sm, int lx, int ly,
                                                    const RefStats& st, float3 rp, float d, float3 n) {
     constexpr int NP = NS / 2;
@@ -440,10 +507,10 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
         const float t = __fdividef(dn, den);
         const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
         const float alpha = t * cl, beta = -t * sm.row_sin[ly + o];
-        pairs_sample<NP>(P, alpha, beta, lx + o, c0);
+        pairs_sample<NP, VA>(P, alpha, beta, lx + o, c0);
 #pragma unroll
         for (int q = 0; q < NP; ++q) SJ[q] = SJJ[q] = SIJ[q] = pair(0.f);
-        if (ODD) c0o = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z);
+        if (ODD) c0o = view_sample<VA>(P.src[NS - 1], X, Y, Z);
     }
     bool valid = true;
 #pragma unroll 1
@@ -468,7 +535,7 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
             const float alpha = t * cl, beta = t * msl;
             const float2 w2 = pair(w), wI2 = pair(wI);
             float2 Jall[NP];
-            pairs_sample<NP>(P, alpha, beta, cx, Jall);
+            pairs_sample<NP, VA>(P, alpha, beta, cx, Jall);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const float2 J = Jall[q];
@@ -479,7 +546,7 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
                 SIJ[q] = fma2(wI2, Jc, SIJ[q]);
             }
             if (ODD) {
-                const float Jc = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z) - c0o;
+                const float Jc = view_sample<VA>(P.src[NS - 1], X, Y, Z) - c0o;
                 const float tw = w * Jc;
                 SJo += tw;
                 SJJo = fmaf(tw, Jc, SJJo);
@@ -520,13 +587,21 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
     return sum / (float)P.best_k;
 }
 
+// The paired form serves exactly known view counts whose views sit in kernel
+// parameters or in shared memory (the batched kernel); the general form the
+// guarded view count and plain-load sources.
+template <class VA>
+constexpr bool paired_views() {
+    return std::is_same<VA, ParamViews>::value || std::is_same<VA, SharedViews>::value;
+}
+
 // The cost used by the per-pixel kernels: the paired form where the views
-// are exactly known and sit in kernel parameters, the general one otherwise.
+// are exactly known, the general one otherwise.
 template <int NS, bool EXACT, class VA, int WIN = 0, class SM = TileSmem>
 __device__ __forceinline__ float cost_of(const PixelParams& P, const SM& sm, int lx, int ly,
                                          const RefStats& st, float3 rp, float d, float3 n) {
-    if constexpr (EXACT && NS >= 2 && std::is_same<VA, ParamViews>::value)
-        return plane_cost_paired<NS, WIN, SM>(P, sm, lx, ly, st, rp, d, n);
+    if constexpr (EXACT && NS >= 2 && paired_views<VA>())
+        return plane_cost_paired<NS, WIN, SM, VA>(P, sm, lx, ly, st, rp, d, n);
     else
         return plane_cost<NS, EXACT, VA, SM>(P, sm, lx, ly, st, rp, d, n);
 }
@@ -561,7 +636,7 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, SM& sm, int b
                                              int iter) {
     stage_tile(P, sm, bx, by);
     __syncthreads();
-    if constexpr (EXACT && NS >= 2 && std::is_same<VA, ParamViews>::value) {
+    if constexpr (EXACT && NS >= 2 && paired_views<VA>()) {
         constexpr int NP = NS / 2;
         static_assert(NP <= MAX_COL_PAIRS, "column table too small");
         const int cols = SM::W + 2 * P.radius;
