@@ -533,11 +533,17 @@ def run_serving(args):
     classes = rng.choice(3, size=n_req, p=weights / weights.sum())
     views = rng.integers(4, 11, size=n_req)
     out = {}
-    for mode, fmt in (("served", "f16"), ("plain", "u8"), ("plain", "f32")):
-        cfs = [ClassFrames(W, H, 24, 2000 + ci, fmt) for ci, (W, H, _) in enumerate(BATCH_CLASSES)]
+    runs = [("served", "f16", pm.PMSP_SCHED_LANES), ("served", "f16", pm.PMSP_SCHED_STEPS), ("plain", "f32", None)]
+    if args.serving_all:
+        runs.append(("plain", "u8", None))
+    frames_of = {}
+    for mode, fmt, sched in runs:
+        if fmt not in frames_of:
+            frames_of[fmt] = [ClassFrames(W, H, 24, 2000 + ci, fmt) for ci, (W, H, _) in enumerate(BATCH_CLASSES)]
+        cfs = frames_of[fmt]
         lat = []
         if mode == "served":
-            ctx = pm.Context(0, stream=None, ring_capacity=64)
+            ctx = pm.Context(0, stream=None, ring_capacity=64, scheduler=sched)
             counters = [0, 0, 0]
             ids = [[], [], []]
             next_id = [0]
@@ -629,17 +635,19 @@ def run_serving(args):
             wall = time.perf_counter() - t0
             ctx.close()
         lat = np.array(lat) * 1e3
-        out[f"{mode}_{fmt}"] = dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-                                    keyframes_per_s=n_req / wall, wall_s=wall)
+        name = f"{mode}_{fmt}" + ("" if sched is None else ("_lanes" if sched == pm.PMSP_SCHED_LANES else "_steps"))
+        out[name] = dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                         keyframes_per_s=n_req / wall, wall_s=wall)
+        print(name, out[name], file=sys.stderr, flush=True)
+    best = min(("served_f16_lanes", "served_f16_steps"), key=lambda k: out[k]["p99_ms"])
     print(json.dumps(dict(
         metric="p50/p99 latency and keyframes/s, Poisson 4/s + 12/s bursts, mixed sizes",
-        value=out["served_f16"]["keyframes_per_s"], unit="keyframes/s", n_gpus=1, steps=n_req, warmup=0,
-        ms_per_step=1e3 * out["served_f16"]["wall_s"] / n_req, higher_is_better=True, scaling="weak",
+        value=out[best]["keyframes_per_s"], unit="keyframes/s", n_gpus=1, steps=n_req, warmup=0,
+        ms_per_step=1e3 * out[best]["wall_s"] / n_req, higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype="f32", data="synthetic",
-        latency_ms=dict(p50=out["served_f16"]["p50_ms"], p99=out["served_f16"]["p99_ms"]),
+        latency_ms=dict(p50=out[best]["p50_ms"], p99=out[best]["p99_ms"]),
         config=dict(workload=f"serving form: {n_req} requests over a 64-frame ring, continuous batching",
-                    image_storage="f16",
-                    plain_fifo_u8=out["plain_u8"], plain_fifo_f32=out["plain_f32"]))))
+                    image_storage="f16", scheduler=best.rsplit("_", 1)[1], runs=out))))
 
 
 def run_pipeline(args):
@@ -732,6 +740,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="keyframe", choices=["keyframe", "batched", "serving", "pipeline"])
     ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--serving-all", action="store_true", help="serving workload: also the uint8 FIFO")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

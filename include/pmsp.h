@@ -127,7 +127,20 @@ typedef struct {
     uint64_t mem_cap_bytes;  /* serving admission cap (0: 40 GiB) */
     int32_t ring_capacity;   /* frames kept in the device ring (0: 64) */
     int32_t max_active;      /* serving slots (0: 32) */
+    int32_t scheduler;       /* pmsp_scheduler of the serving runtime (0: lanes) */
 } pmsp_ctx_opts;
+
+/* Serving schedulers (Sec. III: densification in its own thread, fed by a
+ * keyframe queue). Both admit FIFO under the same rules (slots, memory cap,
+ * resident tiles, depth-map order) and give every request the same maps.
+ *   PMSP_SCHED_LANES  each admitted request's whole launch chain starts on a
+ *                     stream lane of its own; chains of different requests
+ *                     overlap on the device.
+ *   PMSP_SCHED_STEPS  iteration-level: each scheduler step is one persistent
+ *                     launch running the next phase (initialisation colour or
+ *                     half-sweep) of every active request; requests join at
+ *                     the next step and leave after their last phase. */
+typedef enum { PMSP_SCHED_LANES = 0, PMSP_SCHED_STEPS = 1 } pmsp_scheduler;
 
 typedef struct pmsp_ctx pmsp_ctx;
 
@@ -466,7 +479,7 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, rejected;
     uint32_t queued, active;
-    uint64_t steps;               /* requests started on a stream lane so far */
+    uint64_t steps;               /* lanes: requests started on a lane; steps: step launches */
     uint64_t bytes_in_use;        /* maps of admitted and unretrieved requests */
 } pmsp_serving_stats;
 

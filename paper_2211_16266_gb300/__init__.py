@@ -74,7 +74,10 @@ class pmsp_maps(ctypes.Structure):
 
 class pmsp_ctx_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("mem_cap_bytes", ctypes.c_uint64),
-                ("ring_capacity", ctypes.c_int32), ("max_active", ctypes.c_int32)]
+                ("ring_capacity", ctypes.c_int32), ("max_active", ctypes.c_int32), ("scheduler", ctypes.c_int32)]
+
+
+PMSP_SCHED_LANES, PMSP_SCHED_STEPS = 0, 1
 
 
 _P = ctypes.c_void_p
@@ -249,7 +252,8 @@ class Context:
     """Owns a pmsp_ctx. stream: "torch" (default: torch's current stream), a torch.cuda.Stream,
     a raw cudaStream_t int, or None (the context creates its own stream)."""
 
-    def __init__(self, device=0, stream="torch", mem_cap_bytes=0, ring_capacity=0, max_active=0):
+    def __init__(self, device=0, stream="torch", mem_cap_bytes=0, ring_capacity=0, max_active=0,
+                 scheduler=PMSP_SCHED_LANES):
         # default: torch's current stream on `device`, so work is ordered after the
         # torch copies that produce the inputs; None: a private stream
         if isinstance(stream, str) and stream == "torch":
@@ -260,7 +264,7 @@ class Context:
             raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
             if raw == 0:
                 raw = 1  # torch's default stream is the legacy stream (cudaStreamLegacy)
-        opts = pmsp_ctx_opts(device, raw, mem_cap_bytes, ring_capacity, max_active)
+        opts = pmsp_ctx_opts(device, raw, mem_cap_bytes, ring_capacity, max_active, scheduler)
         h = ctypes.c_void_p()
         rc = _lib.pmsp_create(ctypes.byref(h), ctypes.byref(opts))
         if rc != PMSP_OK:

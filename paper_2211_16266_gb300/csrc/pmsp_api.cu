@@ -367,6 +367,7 @@ void pmsp_default_params(pmsp_params* p) {
 int pmsp_create(pmsp_ctx** out, const pmsp_ctx_opts* opts) {
     if (!out) return PMSP_EINVAL;
     *out = nullptr;
+    if (opts && opts->scheduler != PMSP_SCHED_LANES && opts->scheduler != PMSP_SCHED_STEPS) return PMSP_EINVAL;
     pmsp_ctx* c = new (std::nothrow) pmsp_ctx();
     if (!c) return PMSP_ENOMEM;
     c->device = opts ? opts->device : 0;
@@ -389,6 +390,7 @@ int pmsp_create(pmsp_ctx** out, const pmsp_ctx_opts* opts) {
     c->mem_cap = (opts && opts->mem_cap_bytes) ? opts->mem_cap_bytes : (40ull << 30);
     c->ring_capacity = (opts && opts->ring_capacity > 0) ? opts->ring_capacity : 64;
     c->max_active = (opts && opts->max_active > 0) ? opts->max_active : 32;
+    c->scheduler = opts ? opts->scheduler : PMSP_SCHED_LANES;
     e = cudaMalloc(&c->d_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
     if (e != cudaSuccess) {

@@ -65,6 +65,7 @@ struct pmsp_ctx {
     uint64_t mem_cap = 0;
     int ring_capacity = 0;
     int max_active = 0;
+    int scheduler = 0;  // pmsp_scheduler of the serving runtime
     std::vector<pmsp::TexImage> src_tex;  // one texture per source slot
     pmsp::TexImage sample_tex;
     pmsp::DevBuffer ref_stage, map_stage, filter_stage, sample_stage, median_stage;

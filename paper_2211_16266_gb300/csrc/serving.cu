@@ -1,11 +1,13 @@
 // Serving runtime: device frame ring, admission by slots, memory and resident
-// work, and a scheduler thread that starts every admitted request's launch
-// chain on a stream lane of its own, so requests that arrive while others run
-// are admitted as soon as a lane and memory free up and their kernels overlap
-// on the device (continuous batching at the granularity of the half-sweep
-// launches). Paper Sec. III runs densification in its own thread fed by a
-// keyframe queue; this is that thread, reshaped for many concurrent keyframes
-// on one GPU.
+// work, and a scheduler thread with two policies. Lanes: every admitted
+// request's whole launch chain starts on a stream lane of its own, so requests
+// that arrive while others run are admitted as soon as a lane and memory free
+// up and their kernels overlap on the device. Steps (iteration-level
+// continuous batching): each scheduler step is one persistent launch that runs
+// the next phase (initialisation colour or half-sweep) of every active
+// request; requests join at the next step and leave after their last phase.
+// Paper Sec. III runs densification in its own thread fed by a keyframe queue;
+// this is that thread, reshaped for many concurrent keyframes on one GPU.
 //
 // Host waits are bounded: the scheduler polls CUDA events and fails a request
 // with PMSP_ETIMEDOUT when it has not finished within a deadline; pmsp_wait
@@ -64,6 +66,9 @@ struct Request {
     int n_phases = 0;
     size_t bytes = 0, tiles = 0;
     int lane = -1;
+    cudaStream_t stream = nullptr;  // the stream its work runs on (maps are freed in its order)
+    int phase = 0;                  // steps: next phase to launch
+    int slot = -1;                  // steps: its parameter slot on the device
     Clock::time_point admitted;
     DevBuffer maps;        // depth, nx, ny, nz, cost, filtered depth
     cudaEvent_t done = nullptr;
@@ -95,6 +100,21 @@ struct Serving {
     pmsp_serving_stats stats{};
     int sms = 0;
     std::string err;
+    // step scheduler (PMSP_SCHED_STEPS): one stream, per-request parameter slots
+    // on the device, a work list per step staged through two pinned buffers
+    cudaStream_t step_stream = nullptr;
+    PixelParams* d_slots = nullptr;
+    PixelParams* h_slots = nullptr;     // pinned host copies, one per slot
+    std::vector<cudaEvent_t> slot_ev;   // last upload from each host copy
+    std::vector<int> free_slots;
+    DevBuffer d_work;
+    unsigned* d_counter = nullptr;
+    int4* h_work[2] = {nullptr, nullptr};
+    size_t h_work_cap[2] = {0, 0};
+    cudaEvent_t work_ev[2] = {nullptr, nullptr};
+    int work_next = 0;
+    std::deque<cudaEvent_t> inflight;   // completion events of launched steps
+    std::vector<cudaEvent_t> ev_pool;
 };
 
 namespace {
@@ -142,7 +162,7 @@ void release_request(Serving& s, Request* r) {
     s.ring[r->ref].pins--;
     // freed in the order of the stream the request's work ran on, so a request
     // whose launch chain failed part-way cannot have its maps reused under it
-    if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, r->lane >= 0 ? s.lanes[r->lane] : s.upload);
+    if (r->maps.ptr) cudaFreeAsync(r->maps.ptr, r->stream ? r->stream : s.upload);
     if (r->done) cudaEventDestroy(r->done);
     if (r->maps.ptr) s.bytes_in_use -= r->bytes;
     delete r;
@@ -172,17 +192,11 @@ void fill_request(Serving& s, Request* r) {
     r->prob.err = s.ctx->d_err;
 }
 
-// A request's whole launch chain on its lane: initialisation, the red/black
-// half-sweeps, the consistency filter against the named neighbours whose
-// depth maps exist, the copy of its depth into the ring, the completion event.
-int enqueue_request(Serving& s, Request* r, cudaStream_t st) {
-    PixelParams P = r->prob;
+// What follows a request's last phase: the consistency filter against the
+// named neighbours whose depth maps exist, the copy of its depth into the
+// ring, the completion event.
+int enqueue_tail(Serving& s, Request* r, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
-    for (int ph = 0; ph < r->n_phases && e == cudaSuccess; ++ph) {
-        P.colour = ph & 1;
-        P.iter = ph < 2 ? 0 : (ph - 2) >> 1;
-        e = launch_pixel_kernel(P, ph < 2 ? MODE_INIT : MODE_SWEEP, st);
-    }
     const size_t N = (size_t)r->W * r->H;
     float* base = static_cast<float*>(r->maps.ptr);
     float* filtered = base + 5 * N;
@@ -225,6 +239,20 @@ int enqueue_request(Serving& s, Request* r, cudaStream_t st) {
     return e == cudaSuccess ? PMSP_OK : PMSP_ECUDA;
 }
 
+// A request's whole launch chain on its lane: initialisation, the red/black
+// half-sweeps, then the tail.
+int enqueue_request(Serving& s, Request* r, cudaStream_t st) {
+    PixelParams P = r->prob;
+    cudaError_t e = cudaSuccess;
+    for (int ph = 0; ph < r->n_phases && e == cudaSuccess; ++ph) {
+        P.colour = ph & 1;
+        P.iter = ph < 2 ? 0 : (ph - 2) >> 1;
+        e = launch_pixel_kernel(P, ph < 2 ? MODE_INIT : MODE_SWEEP, st);
+    }
+    if (e != cudaSuccess) return PMSP_ECUDA;
+    return enqueue_tail(s, r, st);
+}
+
 DepthUse depth_use(const Request* r) { return DepthUse{r->ref, r->filters.data(), (int)r->filters.size()}; }
 
 // Whether starting r now would let two running chains touch one frame's depth
@@ -236,33 +264,49 @@ bool conflicts_with_running(const Serving& s, const Request* r) {
     return depth_conflict(depth_use(r), running.data(), (int)running.size());
 }
 
+// Retire requests whose completion event has fired (or that overran the
+// deadline). `finished` says whether a request's last work is enqueued.
+template <class Finished>
+void retire(Serving& s, Finished finished) {
+    for (size_t k = 0; k < s.running.size();) {
+        Request* r = s.running[k];
+        if (!finished(r)) {
+            ++k;
+            continue;
+        }
+        // a request whose work could not be enqueued has fail_code set and no
+        // completion event recorded (an unrecorded event would read as complete)
+        const bool broken = r->fail_code != PMSP_OK;
+        const cudaError_t q = broken ? cudaErrorLaunchFailure : cudaEventQuery(r->done);
+        const bool late = q == cudaErrorNotReady &&
+                          Clock::now() - r->admitted > std::chrono::duration<double>(REQUEST_DEADLINE_S);
+        if (q == cudaErrorNotReady && !late) {
+            ++k;
+            continue;
+        }
+        r->status = q == cudaSuccess ? DONE : FAILED;
+        if (q == cudaSuccess) s.ring[r->ref].has_depth = true;  // later filters may read it
+        if (q != cudaSuccess && !broken) {
+            r->fail_code = late ? PMSP_ETIMEDOUT : PMSP_ECUDA;
+            s.err = late ? "request did not finish within the deadline" : cudaGetErrorString(q);
+        }
+        s.stats.completed += q == cudaSuccess;
+        s.running_tiles -= r->tiles;
+        if (!late) {  // a late request keeps its lane or slot blocked
+            if (r->lane >= 0) s.lane_req[r->lane] = nullptr;
+            if (r->slot >= 0) s.free_slots.push_back(r->slot);
+        }
+        s.running.erase(s.running.begin() + k);
+        s.cv_done.notify_all();
+    }
+}
+
 void scheduler(Serving* sp) {
     Serving& s = *sp;
     cudaSetDevice(s.ctx->device);
     std::unique_lock<std::mutex> lk(s.mu);
     for (;;) {
-        // retire requests whose completion event has fired (or that overran the deadline)
-        for (size_t k = 0; k < s.running.size();) {
-            Request* r = s.running[k];
-            const cudaError_t q = cudaEventQuery(r->done);
-            const bool late = q == cudaErrorNotReady &&
-                              Clock::now() - r->admitted > std::chrono::duration<double>(REQUEST_DEADLINE_S);
-            if (q == cudaErrorNotReady && !late) {
-                ++k;
-                continue;
-            }
-            r->status = q == cudaSuccess ? DONE : FAILED;
-            if (q == cudaSuccess) s.ring[r->ref].has_depth = true;  // later filters may read it
-            if (q != cudaSuccess) {
-                r->fail_code = late ? PMSP_ETIMEDOUT : PMSP_ECUDA;
-                s.err = late ? "request did not finish within the deadline" : cudaGetErrorString(q);
-            }
-            s.stats.completed += q == cudaSuccess;
-            s.running_tiles -= r->tiles;
-            if (!late) s.lane_req[r->lane] = nullptr;  // a late request keeps its lane blocked
-            s.running.erase(s.running.begin() + k);
-            s.cv_done.notify_all();
-        }
+        retire(s, [](const Request*) { return true; });
         // admission: FIFO while a lane is free, the maps fit, the resident work allows
         // and no running chain writes or reads a depth map that this one reads or writes
         while (!s.queue.empty()) {
@@ -292,6 +336,7 @@ void scheduler(Serving* sp) {
             s.bytes_in_use += r->bytes;
             fill_request(s, r);
             r->lane = lane;
+            r->stream = st;
             r->admitted = Clock::now();
             if (enqueue_request(s, r, st) != PMSP_OK) {
                 r->status = FAILED;
@@ -317,6 +362,153 @@ void scheduler(Serving* sp) {
     }
 }
 
+// Wait (bounded) until an event has completed, releasing the lock meanwhile.
+bool wait_event_unlocked(Serving& s, std::unique_lock<std::mutex>& lk, cudaEvent_t ev, double seconds) {
+    const auto until = Clock::now() + std::chrono::duration<double>(seconds);
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return true;
+        if (e != cudaErrorNotReady || Clock::now() > until) return false;
+        s.cv_work.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+// One step: the next phase of every active request in one persistent launch
+// over all their tiles (largest request first, row-major tiles), then the tail
+// of each request whose last phase this was. Returns PMSP_OK or PMSP_ECUDA.
+int launch_step(Serving& s, std::unique_lock<std::mutex>& lk) {
+    const cudaStream_t st = s.step_stream;
+    std::vector<Request*> act;
+    for (Request* r : s.running)
+        if (r->phase < r->n_phases) act.push_back(r);
+    if (act.empty()) return PMSP_OK;
+    std::stable_sort(act.begin(), act.end(), [](const Request* a, const Request* b) { return a->W * a->H > b->W * b->H; });
+    size_t n_work = 0;
+    int max_s = 0;
+    for (Request* r : act) {
+        n_work += r->tiles;
+        max_s = std::max(max_s, (int)r->srcs.size());
+    }
+    // the pinned buffer is rewritten only after its previous copy has been read
+    const int b = s.work_next;
+    s.work_next ^= 1;
+    if (s.work_ev[b] && !wait_event_unlocked(s, lk, s.work_ev[b], STEP_DEADLINE_S)) return PMSP_ECUDA;
+    if (s.h_work_cap[b] < n_work) {
+        if (s.h_work[b]) cudaFreeHost(s.h_work[b]);
+        s.h_work[b] = nullptr;
+        s.h_work_cap[b] = 0;
+        if (cudaMallocHost(&s.h_work[b], n_work * sizeof(int4)) != cudaSuccess) return PMSP_ECUDA;
+        s.h_work_cap[b] = n_work;
+    }
+    int4* w = s.h_work[b];
+    for (Request* r : act) {
+        const int tw = (r->W + TILE_W - 1) / TILE_W, th = (r->H + TILE_H - 1) / TILE_H;
+        for (int ty = 0; ty < th; ++ty)
+            for (int tx = 0; tx < tw; ++tx) *w++ = make_int4(r->slot, tx * TILE_W, ty * TILE_H, r->phase);
+    }
+    if (dev_alloc(s.d_work, n_work * sizeof(int4), st) != PMSP_OK) return PMSP_ECUDA;
+    cudaError_t e = cudaMemcpyAsync(s.d_work.ptr, s.h_work[b], n_work * sizeof(int4), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s.work_ev[b], st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.d_counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return PMSP_ECUDA;
+    BatchArgs a;
+    a.problems = s.d_slots;
+    a.work = static_cast<const int4*>(s.d_work.ptr);
+    a.n_work = (int)n_work;
+    a.phase = -1;  // each item's own phase
+    a.counter = s.d_counter;
+    const int bucket = batch_bucket(max_s);
+    const int grid = (int)std::min<size_t>(n_work, (size_t)s.sms * batch_blocks_per_sm(bucket));
+    if (batch_launch(bucket, a, grid, st) != cudaSuccess) return PMSP_ECUDA;
+    for (Request* r : act)
+        if (++r->phase == r->n_phases && enqueue_tail(s, r, st) != PMSP_OK) {
+            r->fail_code = PMSP_ECUDA;
+            return PMSP_ECUDA;
+        }
+    cudaEvent_t ev;
+    if (!s.ev_pool.empty()) {
+        ev = s.ev_pool.back();
+        s.ev_pool.pop_back();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        return PMSP_ECUDA;
+    }
+    if (cudaEventRecord(ev, st) != cudaSuccess) return PMSP_ECUDA;
+    s.inflight.push_back(ev);
+    s.stats.steps++;
+    return PMSP_OK;
+}
+
+// Iteration-level scheduler: admission at step boundaries into parameter
+// slots, at most two steps in flight (phase progress is known on the host, so
+// the next step is enqueued while the current one runs).
+void scheduler_steps(Serving* sp) {
+    Serving& s = *sp;
+    cudaSetDevice(s.ctx->device);
+    std::unique_lock<std::mutex> lk(s.mu);
+    const cudaStream_t st = s.step_stream;
+    for (;;) {
+        while (!s.inflight.empty() && cudaEventQuery(s.inflight.front()) != cudaErrorNotReady) {
+            s.ev_pool.push_back(s.inflight.front());
+            s.inflight.pop_front();
+        }
+        retire(s, [](const Request* r) { return r->phase >= r->n_phases; });
+        // admission: FIFO under the same rules as the lanes (slots, memory cap,
+        // resident tiles, depth-map order), into a free parameter slot
+        while (!s.queue.empty() && !s.free_slots.empty()) {
+            Request* r = s.queue.front();
+            const AdmitState now{(int)s.running.size(), s.ctx->max_active, s.bytes_in_use, s.ctx->mem_cap,
+                                 s.running_tiles, serving_tile_budget(s.sms)};
+            if (admit_block(now, r->bytes, r->tiles, conflicts_with_running(s, r)) != ADMIT_OK) break;
+            if (cudaMallocAsync(&r->maps.ptr, r->bytes, st) != cudaSuccess) {
+                r->maps.ptr = nullptr;
+                break;  // retried on the next pass
+            }
+            r->maps.bytes = r->bytes;
+            if (!r->done && cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) break;
+            const int slot = s.free_slots.back();
+            // the slot's host copy is rewritten only after its last upload has been read
+            if (!wait_event_unlocked(s, lk, s.slot_ev[slot], STEP_DEADLINE_S)) break;
+            s.free_slots.pop_back();
+            s.queue.pop_front();
+            s.bytes_in_use += r->bytes;
+            fill_request(s, r);
+            r->slot = slot;
+            r->stream = st;
+            r->phase = 0;
+            r->admitted = Clock::now();
+            s.h_slots[slot] = r->prob;
+            cudaError_t e = cudaMemcpyAsync(s.d_slots + slot, s.h_slots + slot, sizeof(PixelParams),
+                                            cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaEventRecord(s.slot_ev[slot], st);
+            r->status = ACTIVE;
+            s.running.push_back(r);
+            s.running_tiles += r->tiles;
+            if (e != cudaSuccess) {
+                r->phase = r->n_phases;  // nothing more is launched for it
+                r->fail_code = PMSP_ECUDA;
+                s.err = "parameter upload failed";
+            }
+        }
+        if (s.inflight.size() < 2 && launch_step(s, lk) != PMSP_OK) {
+            // a failed launch fails every request still in its phases
+            s.err = "step launch failed";
+            for (Request* r : s.running)
+                if (r->phase < r->n_phases) {
+                    r->phase = r->n_phases;
+                    r->fail_code = PMSP_ECUDA;
+                }
+        }
+        s.stats.queued = (uint32_t)s.queue.size();
+        s.stats.active = (uint32_t)s.running.size();
+        s.stats.bytes_in_use = s.bytes_in_use;
+        if (s.stop) break;
+        if (s.running.empty())
+            s.cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        else
+            s.cv_work.wait_for(lk, std::chrono::microseconds(100));
+    }
+}
+
 Serving& serving(pmsp_ctx* c) {
     if (!c->serving) {
         Serving* s = new Serving();
@@ -330,7 +522,21 @@ Serving& serving(pmsp_ctx* c) {
             uint64_t keep = UINT64_MAX;  // keep freed request maps in the pool for the next admission
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
-        s->th = std::thread(scheduler, s);
+        if (c->scheduler == PMSP_SCHED_STEPS) {
+            cudaStreamCreateWithFlags(&s->step_stream, cudaStreamNonBlocking);
+            cudaMalloc(&s->d_slots, (size_t)c->max_active * sizeof(PixelParams));
+            cudaMallocHost(&s->h_slots, (size_t)c->max_active * sizeof(PixelParams));
+            cudaMalloc(&s->d_counter, sizeof(unsigned));
+            s->slot_ev.resize(c->max_active);
+            for (int k = 0; k < c->max_active; ++k) {
+                cudaEventCreateWithFlags(&s->slot_ev[k], cudaEventDisableTiming);
+                s->free_slots.push_back(c->max_active - 1 - k);
+            }
+            for (auto& ev : s->work_ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            s->th = std::thread(scheduler_steps, s);
+        } else {
+            s->th = std::thread(scheduler, s);
+        }
         c->serving = s;
     }
     return *c->serving;
@@ -379,6 +585,7 @@ void runtime_shutdown(pmsp_ctx* c) {
         s.cv_work.notify_all();
         if (s.th.joinable()) s.th.join();
         for (cudaStream_t st : s.lanes) cudaStreamSynchronize(st);
+        if (s.step_stream) cudaStreamSynchronize(s.step_stream);
         cudaStreamSynchronize(s.upload);
         for (auto& kv : s.tickets) s.zombies.push_back(kv.second);
         for (Request* r : s.zombies) {
@@ -393,6 +600,19 @@ void runtime_shutdown(pmsp_ctx* c) {
             if (f.depth.ptr) cudaFree(f.depth.ptr);
         }
         for (cudaStream_t st : s.lanes) cudaStreamDestroy(st);
+        if (s.step_stream) {
+            for (cudaEvent_t ev : s.slot_ev) cudaEventDestroy(ev);
+            for (cudaEvent_t ev : s.work_ev) cudaEventDestroy(ev);
+            for (cudaEvent_t ev : s.inflight) cudaEventDestroy(ev);
+            for (cudaEvent_t ev : s.ev_pool) cudaEventDestroy(ev);
+            for (int4* h : s.h_work)
+                if (h) cudaFreeHost(h);
+            if (s.d_work.ptr) cudaFree(s.d_work.ptr);
+            cudaFree(s.d_slots);
+            cudaFreeHost(s.h_slots);
+            cudaFree(s.d_counter);
+            cudaStreamDestroy(s.step_stream);
+        }
         cudaStreamDestroy(s.upload);
         cudaEventDestroy(s.upload_ev);
         delete c->serving;

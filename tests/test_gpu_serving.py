@@ -1,12 +1,15 @@
-"""Serving runtime: frame ring, admission, continuous batching, bounded waits.
+"""Serving runtime: frame ring, admission, continuous batching, bounded waits,
+under both schedulers (stream lanes, and iteration-level steps).
 
 Each request's maps must not depend on what else shares its launches: a
 request served alone, served in a mix of other sizes and view counts, and
-densified by pmsp_densify give the same maps.
+densified by pmsp_densify give the same maps; served maps match the FP64
+oracle's densification and consistency filter.
 """
 import numpy as np
 import pytest
 
+import oracle
 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -45,12 +48,13 @@ def _maps(pm, W, H):
     return pm.Maps.empty(W, H)
 
 
-def test_alone_equals_in_mix_equals_single(pm):
+@pytest.mark.parametrize("sched", [0, 1], ids=["lanes", "steps"])
+def test_alone_equals_in_mix_equals_single(pm, sched):
     import torch
     fa = _frames(384, 192, 7)
     fb = _frames(256, 128, 5, seed_scene=1020)
     fc = _frames(512, 256, 9, seed_scene=1021, fmt="f16")
-    with pm.Context(0, ring_capacity=32) as ctx:
+    with pm.Context(0, scheduler=sched, ring_capacity=32) as ctx:
         _push(pm, ctx, fa, 100)
         _push(pm, ctx, fb, 200)
         _push(pm, ctx, fc, 300)
@@ -79,10 +83,11 @@ def test_alone_equals_in_mix_equals_single(pm):
         assert np.max(np.abs(sc - ac)) <= 1e-6 and np.mean(sd == ad) >= 0.999
 
 
-def test_admission_slots_memory_and_errors(pm):
+@pytest.mark.parametrize("sched", [0, 1], ids=["lanes", "steps"])
+def test_admission_slots_memory_and_errors(pm, sched):
     fa = _frames(256, 128, 5)
     # one slot: requests run one after another and all finish
-    with pm.Context(0, max_active=1, ring_capacity=8) as ctx:
+    with pm.Context(0, scheduler=sched, max_active=1, ring_capacity=8) as ctx:
         _push(pm, ctx, fa, 0)
         ts = [pm.pmsp_submit(ctx, 2, [0, 1, 3, 4], dict(PARAMS, keyframe_id=k)) for k in range(4)]
         for t in ts:
@@ -98,22 +103,23 @@ def test_admission_slots_memory_and_errors(pm):
             pm.pmsp_submit(ctx, 2, [0, 1], dict(PARAMS, best_k=3))
         assert e.value.code == pm.PMSP_EINVAL
     # a memory cap below one request's maps rejects it at submission
-    with pm.Context(0, mem_cap_bytes=256 * 128 * 8, ring_capacity=8) as ctx:
+    with pm.Context(0, scheduler=sched, mem_cap_bytes=256 * 128 * 8, ring_capacity=8) as ctx:
         _push(pm, ctx, fa, 0)
         with pytest.raises(pm.PmspError) as e:
             pm.pmsp_submit(ctx, 2, [0, 1, 3, 4], PARAMS)
         assert e.value.code == pm.PMSP_EADMIT
     # a cap of two requests' maps admits two at a time; all still finish
-    with pm.Context(0, mem_cap_bytes=2 * 256 * 128 * 24, ring_capacity=8) as ctx:
+    with pm.Context(0, scheduler=sched, mem_cap_bytes=2 * 256 * 128 * 24, ring_capacity=8) as ctx:
         _push(pm, ctx, fa, 0)
         ts = [pm.pmsp_submit(ctx, 2, [0, 1, 3, 4], dict(PARAMS, keyframe_id=k)) for k in range(5)]
         for t in ts:
             pm.pmsp_wait(ctx, t, 60000, None)
 
 
-def test_bounded_wait_times_out_then_completes(pm):
+@pytest.mark.parametrize("sched", [0, 1], ids=["lanes", "steps"])
+def test_bounded_wait_times_out_then_completes(pm, sched):
     fa = _frames(1024, 512, 7)
-    with pm.Context(0, ring_capacity=8) as ctx:
+    with pm.Context(0, scheduler=sched, ring_capacity=8) as ctx:
         _push(pm, ctx, fa, 0)
         t = pm.pmsp_submit(ctx, 3, [0, 1, 2, 4, 5, 6], dict(PARAMS, iterations=8))
         with pytest.raises(pm.PmspError) as e:
@@ -123,9 +129,10 @@ def test_bounded_wait_times_out_then_completes(pm):
         pm.pmsp_wait(ctx, t, 120000, None)
 
 
-def test_ring_eviction_and_pinning(pm):
+@pytest.mark.parametrize("sched", [0, 1], ids=["lanes", "steps"])
+def test_ring_eviction_and_pinning(pm, sched):
     fa = _frames(128, 64, 6)
-    with pm.Context(0, ring_capacity=4) as ctx:
+    with pm.Context(0, scheduler=sched, ring_capacity=4) as ctx:
         for k in range(4):
             pm.pmsp_ring_push(ctx, k, *fa[k])
         pm.pmsp_ring_push(ctx, 4, *fa[4])                 # evicts frame 0
@@ -141,9 +148,10 @@ def test_ring_eviction_and_pinning(pm):
         pm.pmsp_ring_push(ctx, 5, *fa[5])                 # frames released with the ticket
 
 
-def test_filter_against_finished_neighbours(pm):
+@pytest.mark.parametrize("sched", [0, 1], ids=["lanes", "steps"])
+def test_filter_against_finished_neighbours(pm, sched):
     fa = _frames(384, 192, 9)
-    with pm.Context(0, ring_capacity=16) as ctx:
+    with pm.Context(0, scheduler=sched, ring_capacity=16) as ctx:
         _push(pm, ctx, fa, 0)
         nb = {}
         for k in (2, 3, 5, 6):
@@ -161,7 +169,7 @@ def test_filter_against_finished_neighbours(pm):
         assert 0.2 < np.mean(out.depth > 0) < 1.0
     # submitted together, the filtered request starts only after its neighbours have
     # finished (their maps are written on other lanes), so the result is the same
-    with pm.Context(0, ring_capacity=16) as ctx:
+    with pm.Context(0, scheduler=sched, ring_capacity=16) as ctx:
         _push(pm, ctx, fa, 0)
         tickets = []
         for k in (2, 3, 5, 6):
@@ -172,3 +180,66 @@ def test_filter_against_finished_neighbours(pm):
             pm.pmsp_wait(ctx, tk, 60000, None)
         out2 = pm.pmsp_wait(ctx, t, 60000, _maps(pm, 384, 192))
         assert np.array_equal(out2.depth, want)
+
+
+@pytest.mark.parametrize("sched", [0, 1], ids=["lanes", "steps"])
+def test_served_in_a_mix_matches_the_oracle(pm, sched):
+    """Requests at 256x128 (2 sources, 7x7 dense window, 4 iterations, best-1)
+    and 384x192 (6 sources, 11x11/2, best-3), served together with others,
+    against orc_densify at the densification's bar (cost 1e-4, range 0.5 %, on
+    99.5 % of pixels)."""
+    fa = _frames(384, 192, 7)
+    fb = _frames(256, 128, 3, seed_scene=1020)
+    fc = _frames(512, 256, 5, seed_scene=1021, fmt="f16")
+    pa = dict(PARAMS, keyframe_id=31)
+    pb = dict(PARAMS, patch_w=7, patch_stride=1, best_k=1, sigma_color=0.0, sigma_space=0.0, keyframe_id=32)
+    with pm.Context(0, scheduler=sched, ring_capacity=32) as ctx:
+        _push(pm, ctx, fa, 100)
+        _push(pm, ctx, fb, 200)
+        _push(pm, ctx, fc, 300)
+        ta = pm.pmsp_submit(ctx, 103, [100, 101, 102, 104, 105, 106], pa)
+        t_other = pm.pmsp_submit(ctx, 302, [300, 301, 303, 304], dict(PARAMS, keyframe_id=33))
+        tb = pm.pmsp_submit(ctx, 201, [200, 202], pb)
+        got = {"a": pm.pmsp_wait(ctx, ta, 60000, _maps(pm, 384, 192)),
+               "b": pm.pmsp_wait(ctx, tb, 60000, _maps(pm, 256, 128))}
+        pm.pmsp_wait(ctx, t_other, 60000, None)
+    cases = {"a": (fa, 3, (0, 1, 2, 4, 5, 6), pa), "b": (fb, 1, (0, 2), pb)}
+    for key, (fr, ref, srcs, params) in cases.items():
+        ob = oracle.Problem(fr[ref][0], fr[ref][1], [fr[j][0] for j in srcs], [fr[j][1] for j in srcs], **params)
+        od, on, oc = ob.densify()
+        gd, gn, gc = (a.astype(np.float64) for a in got[key].numpy())
+        depth_ok = np.mean(np.abs(gd - od) / od <= 5e-3)
+        cost_ok = np.mean(np.abs(gc - oc) <= 1e-4)
+        print(f"served {key} ({sched}): depth parity {depth_ok:.4f} cost parity {cost_ok:.4f}")
+        assert depth_ok >= 0.995 and cost_ok >= 0.995
+
+
+@pytest.mark.parametrize("sched", [0, 1], ids=["lanes", "steps"])
+def test_served_filter_matches_the_oracle(pm, sched):
+    """A request filtered against two finished neighbours (1 px, at least one
+    agreeing view): its depth equals orc_consistency_filter applied to the same
+    request's unfiltered depth and the neighbours' served depths, on every pixel
+    whose decisions are clear of their thresholds (margin 1e-3)."""
+    fa = _frames(384, 192, 7)
+    with pm.Context(0, scheduler=sched, ring_capacity=16) as ctx:
+        _push(pm, ctx, fa, 0)
+        nb = {}
+        for k in (2, 4):
+            srcs = [j for j in range(k - 2, k + 3) if j != k]
+            nb[k] = pm.pmsp_wait(ctx, pm.pmsp_submit(ctx, k, srcs, dict(PARAMS, keyframe_id=k)), 60000,
+                                 _maps(pm, 384, 192))
+        srcs = [1, 2, 4, 5]
+        t = pm.pmsp_submit(ctx, 3, srcs, dict(PARAMS, keyframe_id=3), filter_frames=[2, 4], max_reproj_px=1.0,
+                           min_views=1)
+        out = pm.pmsp_wait(ctx, t, 60000, _maps(pm, 384, 192))
+        raw = pm.pmsp_wait(ctx, pm.pmsp_submit(ctx, 3, srcs, dict(PARAMS, keyframe_id=3)), 60000,
+                           _maps(pm, 384, 192))
+    o_out, _, margin = oracle.consistency_filter(raw.depth.astype(np.float64), fa[3][1],
+                                                 [nb[k].depth.astype(np.float64) for k in (2, 4)],
+                                                 [fa[k][1] for k in (2, 4)], 1.0, 1)
+    clear = margin > 1e-3
+    assert np.mean(clear) > 0.98
+    assert np.array_equal(out.depth[clear] > 0, o_out[clear] > 0)
+    kept = out.depth > 0
+    assert np.array_equal(out.depth[kept], raw.depth[kept])
+    assert 0.2 < np.mean(kept) < 1.0
