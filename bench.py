@@ -498,7 +498,8 @@ def run_batched(args):
                 stream.synchronize()
                 acc["batched_f16"] = accuracy(outs, gts)
                 res["tuning"] = dict(strategy=tuning.strategy, blocks_per_sm=tuning.blocks_per_sm,
-                                     order=tuning.order, patch_stride=tuning.patch_stride, tile=tuning.tile)
+                                     order=tuning.order, patch_stride=tuning.patch_stride, tile=tuning.tile,
+                                     tpp=tuning.tpp)
             res[f"plain_{fmt}"] = timed(plain, max(2, args.steps))
             stream.synchronize()
             acc[f"plain_{fmt}"] = accuracy(outs, gts)

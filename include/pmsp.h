@@ -392,6 +392,11 @@ typedef struct {
     int32_t tile;          /* strategy 1, half-sweeps with an 11x11/2 or 7x7/1 window: tile of
                               reference pixels per 128-thread block, 0: 32x8, 1: 64x4, 2: 16x16
                               (every shape computes the same numbers) */
+    int32_t tpp;           /* strategy 1, half-sweeps of keyframes with 2 or more sources:
+                              threads per pixel, 0 or 1: one; 2 or 4: the pixel's view pairs
+                              (views, above 10 sources) split over 2 or 4 warps that exchange
+                              their view costs through shared memory; the same numbers, fewer
+                              registers per thread (tile 32x4 or 32x2, `tile` ignored) */
 } pmsp_tuning;
 
 #define PMSP_BATCH_GRAPH 1u /* capture the batch in a CUDA graph and replay it when the identical

@@ -1,5 +1,5 @@
 // Instantiation of the per-pixel kernels for 11 to 16 source views.
-#include "pixel_kernel.cuh"
+#include "pixel_split.cuh"
 
 namespace pmsp {
 template cudaError_t launch_pixel_kernel_ns<16, false>(const PixelParams&, int, cudaStream_t);

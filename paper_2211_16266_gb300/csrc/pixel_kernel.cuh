@@ -53,13 +53,14 @@ constexpr int min_blocks_for(int ns) { return ns <= 4 ? 8 : ns <= 6 ? 7 : ns <= 
 constexpr int pixel_min_blocks(int ns) { return ns <= 6 ? 7 : ns <= 8 ? 5 : 4; }
 
 // Shared memory of one tile of TW x TH reference pixels (halo included);
-// every shape has (TW / 2) x TH = 128 threads, one per pixel of one colour.
-template <int TW, int TH>
+// every shape has (TW / 2) x TH pixels of one colour and TPP threads per
+// pixel, 128 threads in all.
+template <int TW, int TH, int TPP = 1>
 struct TileSmemT {
     static constexpr int W = TW, H = TH;
     static constexpr int PITCH = TW + 2 * MAX_HALO, ROWS = TH + 2 * MAX_HALO;
     static constexpr int THREADS = (TW / 2) * TH;
-    static_assert(THREADS == BLOCK_THREADS, "every tile shape runs 128 threads");
+    static_assert(THREADS * TPP == BLOCK_THREADS, "every tile shape runs 128 threads");
     float ref[ROWS * PITCH];             // normalised intensities, halo included
     float row_cos[ROWS], row_sin[ROWS];  // cos lat, sin lat
     float col_sin[PITCH], col_cos[PITCH];  // sin lon, cos lon
@@ -782,6 +783,10 @@ __host__ __device__ inline int window_of(const PixelParams& p) {
     return 0;
 }
 
+// Half-sweeps with 2 or 4 threads (warps) per pixel, pixel_split.cuh.
+template <int NS, bool EXACT>
+cudaError_t launch_split_sweep(const PixelParams& p, cudaStream_t stream);
+
 template <int NS, bool EXACT>
 cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t stream) {
     const dim3 grid((p.W + TILE_W - 1) / TILE_W, (p.H + TILE_H - 1) / TILE_H);
@@ -789,6 +794,9 @@ cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t 
         case MODE_COST: pixel_kernel<NS, EXACT, MODE_COST><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
         case MODE_INIT: pixel_kernel<NS, EXACT, MODE_INIT><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
         default:
+            // views split over several warps per pixel (a tuning choice; same maps)
+            if constexpr (NS >= 2)
+                if (p.tpp > 1) return launch_split_sweep<NS, EXACT>(p, stream);
             // the half-sweep dominates the run time: fixed-window instances for the
             // paired path (exact view counts of at least 2), in three tile shapes
             if constexpr (EXACT && NS >= 2) {
