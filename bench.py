@@ -8,9 +8,14 @@ Inputs are seeded synthetic panoramas (scenes/) already resident in HBM;
 the L2 is flushed between timed steps and each step is timed with CUDA
 events on the launching stream.
 
+At N = 1 the line also carries the batched form (32 keyframes of mixed sizes in
+one batch, fp16 images, against the plain per-keyframe path with fp32 images)
+and the served form (300 Poisson requests over a 64-frame fp16 ring against a
+FIFO of the plain fp32 path), each with its own config (--no-extras skips them).
+
 --impl reference times the CPU oracle on the same workload (bounded sample
 per step: random initialisation plus one half-sweep of the 1920x960 frame,
-scaled to a keyframe).
+scaled to a keyframe, plus the consistency filter).
 """
 from __future__ import annotations
 
@@ -263,14 +268,45 @@ def run_gpu(args):
                                    sfu_frac=4 * achieved / peaks["sfu_per_s"]),
                                measured_peaks=peaks)
         res["e2e"] = e2e
+        gt = frames[KF].range
+        dk = out.depth.cpu().numpy()
+        res["ground_truth"] = dict(within_5pct=float(np.mean(np.abs(dk - gt) < 0.05 * gt)),
+                                   within_1pct=float(np.mean(np.abs(dk - gt) < 0.01 * gt)),
+                                   of="the keyframe's range map before the filter, against the rendered range")
         if not args.no_cpu_baseline and ws == 1:
             nb_np = [nb_maps[k].depth.cpu().numpy() for k in NB]
             res["cpu_baseline"] = cpu_baseline(frames, KF, params, out.depth.cpu().numpy(), nb_np, NB)
+        if ws == 1 and not args.no_extras:
+            res.update(extra_forms(args))
         print(json.dumps(res))
     ctx.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# The autotuner's pick on the 32-keyframe fp16 batch (bench.py --workload batched):
+# pmsp_tuning(blocks_per_sm, order, patch_stride, strategy, tile, tpp).
+BATCH_TUNING = (0, 0, 0, 1, 0, 1)
+
+
+def extra_forms(args):
+    """The batched and served forms beside the keyframe line (N = 1 only): the 32-keyframe
+    batch in fp16 against the plain per-keyframe path with fp32 images, and the served
+    fp16 ring (lanes) against the plain fp32 FIFO on the Poisson trace, with ground-truth
+    accuracy and latency."""
+    import paper_2211_16266_gb300 as pm
+    forms, used = batched_forms(formats=("f16", "f32"), reps=3, tuning=BATCH_TUNING)
+    runs = serving_runs(args.requests, [("served", "f16", pm.PMSP_SCHED_LANES), ("plain", "f32", None)])
+    return dict(
+        batched=dict(metric=BATCHED_METRIC, unit="keyframes/s", value=forms["batched_f16"]["keyframes_per_s"],
+                     config=dict(workload="32 mixed keyframes in one batch, CUDA graph, fp16 images", tuning=used),
+                     forms=forms),
+        serving=dict(metric=SERVING_METRIC, unit="keyframes/s", value=runs["served_f16_lanes"]["keyframes_per_s"],
+                     latency_ms=dict(p50=runs["served_f16_lanes"]["p50_ms"], p99=runs["served_f16_lanes"]["p99_ms"]),
+                     config=dict(workload=f"{args.requests} Poisson requests over a 64-frame fp16 ring, lanes "
+                                          "scheduler, 40 GB admission cap"),
+                     runs=runs))
 
 
 def time_sweeps(pm, ctx, stream, kf_args, params, out, flush):
@@ -440,16 +476,18 @@ def batched_problems(fmt, seed=3000, with_range=False):
     return out
 
 
-def run_batched(args):
-    """Config: 32 mixed keyframes in one batch (persistent/concurrent launches, CUDA graph,
-    autotuned), FP16 storage, against the plain per-keyframe path on the same keyframes with
-    uint8, fp16 and fp32 images; ground-truth accuracy of each (share of pixels within 1 %)."""
+def batched_forms(formats=("f16", "u8", "f32"), reps=3, tuning=None):
+    """The 32-keyframe mix in one batch (CUDA graph; autotuned when `tuning` is None),
+    fp16 storage, and the plain per-keyframe path on the same keyframes with each image
+    format in `formats`; per form its median time, keyframes/s and share of pixels within
+    1 % of the rendered range. Returns (forms, tuning used)."""
     import torch
     import paper_2211_16266_gb300 as pm
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     ctx = pm.Context(0, stream=stream)
     res, acc = {}, {}
+    used = None
 
     def accuracy(outs, gts):
         good = total = 0
@@ -459,11 +497,12 @@ def run_batched(args):
             total += gt.size
         return good / total
 
-    for fmt in ("f16", "u8", "f32"):
+    for fmt in formats:
         probs = batched_problems(fmt, with_range=True)
         gts = [p[3] for p in probs]
         to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         cache = {}
+
         def d(im):
             key = id(im)
             if key not in cache:
@@ -474,11 +513,11 @@ def run_batched(args):
         with torch.cuda.stream(stream):
             outs = [pm.Maps.empty(it[0].shape[1], it[0].shape[0], device=dev) for it in items]
 
-            def timed(fn, reps):
+            def timed(fn, n):
                 fn()
                 stream.synchronize()
                 ts = []
-                for _ in range(reps):
+                for _ in range(n):
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     a.record(stream)
                     fn()
@@ -492,38 +531,45 @@ def run_batched(args):
                     pm.pmsp_densify(ctx, *it, out=o)
             if fmt == "f16":
                 batch = pm.Batch([(*it, o) for it, o in zip(items, outs)])
-                tuning = pm.pmsp_autotune(ctx, batch, 0.0)
-                res["batched_f16"] = timed(lambda: pm.pmsp_densify_batch(ctx, batch, pm.PMSP_BATCH_GRAPH, tuning),
-                                           max(2, args.steps))
+                t = pm.pmsp_autotune(ctx, batch, 0.0) if tuning is None else pm.pmsp_tuning(*tuning)
+                res["batched_f16"] = timed(lambda: pm.pmsp_densify_batch(ctx, batch, pm.PMSP_BATCH_GRAPH, t), reps)
                 stream.synchronize()
                 acc["batched_f16"] = accuracy(outs, gts)
-                res["tuning"] = dict(strategy=tuning.strategy, blocks_per_sm=tuning.blocks_per_sm,
-                                     order=tuning.order, patch_stride=tuning.patch_stride, tile=tuning.tile,
-                                     tpp=tuning.tpp)
-            res[f"plain_{fmt}"] = timed(plain, max(2, args.steps))
+                used = dict(blocks_per_sm=t.blocks_per_sm, order=t.order, patch_stride=t.patch_stride,
+                            strategy=t.strategy, tile=t.tile, tpp=t.tpp)
+            res[f"plain_{fmt}"] = timed(plain, reps)
             stream.synchronize()
             acc[f"plain_{fmt}"] = accuracy(outs, gts)
-    n = sum(c for _, _, c in BATCH_CLASSES)
-    forms = {k: dict(ms=res[k], keyframes_per_s=n / (res[k] / 1e3), within_1pct_of_gt=acc[k])
-             for k in ("batched_f16", "plain_u8", "plain_f16", "plain_f32")}
-    print(json.dumps(dict(
-        metric="keyframes/s, 32 mixed keyframes (12x960x480, 14x1920x960, 6x3840x1920), 4-10 views",
-        value=n / (res["batched_f16"] / 1e3), unit="keyframes/s", n_gpus=1, steps=args.steps, warmup=1,
-        ms_per_step=res["batched_f16"], higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="f32", data="synthetic",
-        config=dict(workload="batched form: one batch of 32 keyframes, CUDA graph, autotuned", image_storage="f16",
-                    tuning=res["tuning"], forms=forms))))
     ctx.close()
+    n = sum(c for _, _, c in BATCH_CLASSES)
+    forms = {k: dict(ms=res[k], keyframes_per_s=n / (res[k] / 1e3), within_1pct_of_gt=acc[k]) for k in res}
+    return forms, used
 
 
-def run_serving(args):
-    """Config: Poisson requests (4/s, 1-s bursts at 12/s every 20 s) of mixed sizes served by
-    continuous batching over a 64-frame ring (FP16), against a FIFO of the plain
-    per-keyframe path (uint8 and fp32 images) on the same arrival trace."""
+BATCHED_METRIC = "keyframes/s, 32 mixed keyframes (12x960x480, 14x1920x960, 6x3840x1920), 4-10 views"
+
+
+def run_batched(args):
+    """Config: 32 mixed keyframes in one batch (persistent/concurrent launches, CUDA graph,
+    autotuned), FP16 storage, against the plain per-keyframe path on the same keyframes with
+    uint8, fp16 and fp32 images; ground-truth accuracy of each (share of pixels within 1 %)."""
+    forms, used = batched_forms(reps=max(2, args.steps))
+    print(json.dumps(dict(
+        metric=BATCHED_METRIC, value=forms["batched_f16"]["keyframes_per_s"], unit="keyframes/s", n_gpus=1,
+        steps=args.steps, warmup=1, ms_per_step=forms["batched_f16"]["ms"], higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f32", data="synthetic",
+        config=dict(workload="batched form: one batch of 32 keyframes, CUDA graph, autotuned", image_storage="f16",
+                    tuning=used, forms=forms))))
+
+
+def serving_runs(n_req, runs):
+    """Poisson requests (4/s, 1-s bursts at 12/s every 20 s, seed 3000) of the batched mix's
+    sizes and 4-10 views; each run is ("served", format, scheduler) over a 64-frame ring or
+    ("plain", format, None), a FIFO of the plain per-keyframe path on the same arrivals.
+    Returns p50/p99 latency (arrival to maps on the host) and keyframes/s per run."""
     import threading
     import torch
     import paper_2211_16266_gb300 as pm
-    n_req = args.requests
     rng = np.random.default_rng(3000)
     t, arrivals = 0.0, []
     while len(arrivals) < n_req:
@@ -534,9 +580,6 @@ def run_serving(args):
     classes = rng.choice(3, size=n_req, p=weights / weights.sum())
     views = rng.integers(4, 11, size=n_req)
     out = {}
-    runs = [("served", "f16", pm.PMSP_SCHED_LANES), ("served", "f16", pm.PMSP_SCHED_STEPS), ("plain", "f32", None)]
-    if args.serving_all:
-        runs.append(("plain", "u8", None))
     frames_of = {}
     for mode, fmt, sched in runs:
         if fmt not in frames_of:
@@ -640,9 +683,26 @@ def run_serving(args):
         out[name] = dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                          keyframes_per_s=n_req / wall, wall_s=wall)
         print(name, out[name], file=sys.stderr, flush=True)
+    return out
+
+
+SERVING_METRIC = "p50/p99 latency and keyframes/s, Poisson 4/s + 12/s bursts, mixed sizes"
+
+
+def run_serving(args):
+    """Config: Poisson requests (4/s, 1-s bursts at 12/s every 20 s) of mixed sizes served by
+    continuous batching over a 64-frame ring (FP16), with either scheduler, against a FIFO
+    of the plain per-keyframe path (fp32, and with --serving-all uint8, images) on the same
+    arrival trace."""
+    import paper_2211_16266_gb300 as pm
+    n_req = args.requests
+    runs = [("served", "f16", pm.PMSP_SCHED_LANES), ("served", "f16", pm.PMSP_SCHED_STEPS), ("plain", "f32", None)]
+    if args.serving_all:
+        runs.append(("plain", "u8", None))
+    out = serving_runs(n_req, runs)
     best = min(("served_f16_lanes", "served_f16_steps"), key=lambda k: out[k]["p99_ms"])
     print(json.dumps(dict(
-        metric="p50/p99 latency and keyframes/s, Poisson 4/s + 12/s bursts, mixed sizes",
+        metric=SERVING_METRIC,
         value=out[best]["keyframes_per_s"], unit="keyframes/s", n_gpus=1, steps=n_req, warmup=0,
         ms_per_step=1e3 * out[best]["wall_s"] / n_req, higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype="f32", data="synthetic",
@@ -748,6 +808,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="keyframe workload: skip the batched and served forms run after it at N = 1")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
