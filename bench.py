@@ -562,6 +562,49 @@ def run_batched(args):
                     tuning=used, forms=forms))))
 
 
+def run_batched_uniform(args):
+    """Config: 4 keyframes at 960x480 with 6 sources each (921,600 pixels, as many as one
+    1920x960 keyframe), 11x11/2, best-3, 2 iterations, uint8: the persistent strategy (one
+    launch per phase over every keyframe's tiles) against per-keyframe chains, best of 5."""
+    import torch
+    import scenes
+    import paper_2211_16266_gb300 as pm
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pm.Context(0, stream=stream)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    items = []
+    for k in range(4):
+        p = scenes.trajectory_problem(960, 480, 6, offset=k, with_range=False)
+        prm = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=2, best_k=3, sigma_color=0.2,
+                   sigma_space=3.0, n_refine=6, neighbor_table=0, seed=42, keyframe_id=k)
+        with torch.cuda.stream(stream):
+            out = pm.Maps.empty(960, 480, device=dev)
+        items.append((d(p.ref.image), (p.ref.R, p.ref.t), [d(f.image) for f in p.srcs],
+                      [(f.R, f.t) for f in p.srcs], prm, out))
+    batch = pm.Batch(items)
+    res = {}
+    for name, t in [("persistent", pm.pmsp_tuning(0, 0, 0, 0, 0, 1)), ("chains", pm.pmsp_tuning(0, 0, 0, 1, 0, 1))]:
+        with torch.cuda.stream(stream):
+            pm.pmsp_densify_batch(ctx, batch, 0, t)
+            stream.synchronize()
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pm.pmsp_densify_batch(ctx, batch, 0, t)
+                e1.record(stream)
+                stream.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        res[name] = min(ts)
+    ctx.close()
+    print(json.dumps(dict(metric="ms per batch, 4 keyframes 960x480, 6 views, 2 iterations", unit="ms",
+                          higher_is_better=False, value=res["persistent"], data="synthetic",
+                          config=dict(workload="uniform batch: persistent strategy vs per-keyframe chains",
+                                      image_storage="u8"),
+                          ms=res)))
+
+
 def serving_runs(n_req, runs):
     """Poisson requests (4/s, 1-s bursts at 12/s every 20 s, seed 3000) of the batched mix's
     sizes and 4-10 views; each run is ("served", format, scheduler) over a 64-frame ring or
@@ -799,7 +842,8 @@ def run_pipeline(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="keyframe", choices=["keyframe", "batched", "serving", "pipeline"])
+    ap.add_argument("--workload", default="keyframe",
+                    choices=["keyframe", "batched", "batched-uniform", "serving", "pipeline"])
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--serving-all", action="store_true", help="serving workload: also the uint8 FIFO")
     ap.add_argument("--gpus", type=int, default=1)
@@ -818,6 +862,8 @@ def main():
     __graft_entry__.build()
     if args.workload == "batched":
         run_batched(args)
+    elif args.workload == "batched-uniform":
+        run_batched_uniform(args)
     elif args.workload == "serving":
         run_serving(args)
     elif args.workload == "pipeline":
