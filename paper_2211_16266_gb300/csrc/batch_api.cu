@@ -220,8 +220,11 @@ static int build_plan(pmsp_ctx* c, BatchEngine& b, const pmsp_batch_item* items,
         for (int i : ids) {
             if (ph >= 2 + 2 * items[i].params.iterations) continue;
             const int tw = (items[i].ref.w + TILE_W - 1) / TILE_W, th = (items[i].ref.h + TILE_H - 1) / TILE_H;
-            for (int ty = 0; ty < th; ++ty)
-                for (int tx = 0; tx < tw; ++tx) per[i].push_back(make_int4(i, tx * TILE_W, ty * TILE_H, ph));
+            for (int L = 0; L < tw * th; ++L) {  // strips of tile rows, as the single-keyframe launches walk them
+                int tx, ty;
+                tile_of_block(tw, th, L, tx, ty);
+                per[i].push_back(make_int4(i, tx * TILE_W, ty * TILE_H, ph));
+            }
         }
         if (t.order == 1) {
             bool more = true;

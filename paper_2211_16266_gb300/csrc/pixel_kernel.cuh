@@ -732,24 +732,6 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, SM& sm, int b
     P.cost[i] = bc;
 }
 
-// Tile of block L in a gx x gy grid: strips of STRIP tile rows, walked column by
-// column, so blocks that run at the same time cover a compact region and their
-// gathers share the texture cache (L1 hit rate 91 % -> 95 %, half-sweep -1.7 %).
-// The rows left below the last full strip are walked row by row. A bijection of
-// [0, gx * gy).
-__device__ __forceinline__ void tile_of_block(int gx, int gy, int L, int& tx, int& ty) {
-    constexpr int STRIP = 8;
-    const int full = (gy / STRIP) * STRIP * gx;
-    if (L < full) {
-        const int strip = L / (gx * STRIP), idx = L - strip * gx * STRIP;
-        tx = idx / STRIP;
-        ty = strip * STRIP + idx % STRIP;
-    } else {
-        tx = (L - full) % gx;
-        ty = (gy / STRIP) * STRIP + (L - full) / gx;
-    }
-}
-
 template <int NS, bool EXACT, int MODE, int WIN = 0, int TS = 0>
 __global__ void __launch_bounds__(BLOCK_THREADS, pixel_min_blocks(NS)) pixel_kernel(const __grid_constant__ PixelParams P) {
     using SM = typename TileShape<TS>::Smem;

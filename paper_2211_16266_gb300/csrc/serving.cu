@@ -374,7 +374,7 @@ bool wait_event_unlocked(Serving& s, std::unique_lock<std::mutex>& lk, cudaEvent
 }
 
 // One step: the next phase of every active request in one persistent launch
-// over all their tiles (largest request first, row-major tiles), then the tail
+// over all their tiles (largest request first, strips of tile rows), then the tail
 // of each request whose last phase this was. Returns PMSP_OK or PMSP_ECUDA.
 int launch_step(Serving& s, std::unique_lock<std::mutex>& lk) {
     const cudaStream_t st = s.step_stream;
@@ -403,8 +403,11 @@ int launch_step(Serving& s, std::unique_lock<std::mutex>& lk) {
     int4* w = s.h_work[b];
     for (Request* r : act) {
         const int tw = (r->W + TILE_W - 1) / TILE_W, th = (r->H + TILE_H - 1) / TILE_H;
-        for (int ty = 0; ty < th; ++ty)
-            for (int tx = 0; tx < tw; ++tx) *w++ = make_int4(r->slot, tx * TILE_W, ty * TILE_H, r->phase);
+        for (int L = 0; L < tw * th; ++L) {  // strips of tile rows (texture-cache locality)
+            int tx, ty;
+            tile_of_block(tw, th, L, tx, ty);
+            *w++ = make_int4(r->slot, tx * TILE_W, ty * TILE_H, r->phase);
+        }
     }
     if (dev_alloc(s.d_work, n_work * sizeof(int4), st) != PMSP_OK) return PMSP_ECUDA;
     cudaError_t e = cudaMemcpyAsync(s.d_work.ptr, s.h_work[b], n_work * sizeof(int4), cudaMemcpyHostToDevice, st);
