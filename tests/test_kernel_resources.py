@@ -50,7 +50,7 @@ def test_six_view_instances_stay_within_the_measured_budget(tmp_path):
     for name, v in pixel.items():
         assert v["regs"] <= 72, (name, v)              # 7 blocks x 128 threads per SM
         # at most 292 B of spill stores + loads in the measured build: issuing each view
-        # pair's gathers right after its coordinates spills a few more values (outside
-        # the per-sample arithmetic) and measured 1.5 % faster than without
+        # pair's gathers right after its coordinates spills a few more values and
+        # measured 1.5 % faster than without
         assert v["spill"] <= 300, (name, v)
         assert v["smem"] * 7 <= 228 * 1024, (name, v)  # 7 blocks fit the SM's shared memory
