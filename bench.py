@@ -9,9 +9,11 @@ the L2 is flushed between timed steps and each step is timed with CUDA
 events on the launching stream.
 
 At N = 1 the line also carries the batched form (32 keyframes of mixed sizes in
-one batch, fp16 images, against the plain per-keyframe path with fp32 images)
-and the served form (300 Poisson requests over a 64-frame fp16 ring against a
-FIFO of the plain fp32 path), each with its own config (--no-extras skips them).
+one batch, fp16 images, against the plain per-keyframe path with fp32 images),
+the served form (300 Poisson requests over a 64-frame fp16 ring against a FIFO
+of the plain fp32 path) and the precision forms (one 3840x1920 keyframe with 8
+sources stored as fp32, fp16 and uint8), each with its own config (--no-extras
+skips them).
 
 --impl reference times the CPU oracle on the same workload (bounded sample
 per step: random initialisation plus one half-sweep of the 1920x960 frame,
@@ -285,6 +287,57 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def precision_forms(reps=3, n_sample=300):
+    """The 3840x1920 precision workload (8 sources, 8-bit texture + N(0, 2 DN) noise,
+    11x11/2, 8 iterations, best-3) rendered once and stored as fp32 (render / 255), fp16
+    (the same minus 0.5, centred) and uint8 (the render quantised): per form the
+    keyframe time (median of `reps`, CUDA events), the share of pixels within 5 % and 1 %
+    of the rendered range, and the share of `n_sample` seeded pixels whose stored cost is
+    within 1e-4 of the FP64 oracle's cost of the stored plane."""
+    import torch
+    import oracle
+    import scenes
+    import paper_2211_16266_gb300 as pm
+    base = scenes.config2(fmt="f32")
+    params = base.params
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pm.Context(0, stream=stream)
+    conv = {"f32": lambda im: im,
+            "f16": lambda im: (im - 0.5).astype(np.float16),
+            "u8": lambda im: np.clip(np.rint(im * 255.0), 0, 255).astype(np.uint8)}
+    gt = base.ref.range
+    H, W = gt.shape
+    rng = np.random.default_rng(6)
+    us, vs = rng.integers(0, W, n_sample), rng.integers(0, H, n_sample)
+    out = {}
+    for fmt, f in conv.items():
+        ref, srcs = f(base.ref.image), [f(fr.image) for fr in base.srcs]
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        args = (d(ref), (base.ref.R, base.ref.t), [d(x) for x in srcs], [(fr.R, fr.t) for fr in base.srcs])
+        with torch.cuda.stream(stream):
+            maps = pm.Maps.empty(W, H, device=dev)
+            pm.pmsp_densify(ctx, *args, params, out=maps)
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pm.pmsp_densify(ctx, *args, params, out=maps)
+                b.record(stream)
+                ts.append((a, b))
+        stream.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in ts]))
+        dep, nrm, cst = (x.astype(np.float64) for x in maps.numpy())
+        pb = oracle.Problem(ref, (base.ref.R, base.ref.t), srcs, [(fr.R, fr.t) for fr in base.srcs], **params)
+        errs = np.array([abs(pb.cost(u, v, dep[v, u], nrm[:, v, u]) - cst[v, u]) for u, v in zip(us, vs)])
+        out[fmt] = dict(ms=ms, keyframes_per_s=1e3 / ms,
+                        within_5pct_of_gt=float(np.mean(np.abs(dep - gt) < 0.05 * gt)),
+                        within_1pct_of_gt=float(np.mean(np.abs(dep - gt) < 0.01 * gt)),
+                        stored_cost_within_1e4_of_fp64_oracle=float(np.mean(errs <= 1e-4)))
+    ctx.close()
+    return out
+
+
 # The autotuner's pick on the 32-keyframe fp16 batch (bench.py --workload batched):
 # pmsp_tuning(blocks_per_sm, order, patch_stride, strategy, tile, tpp).
 BATCH_TUNING = (0, 0, 0, 1, 0, 1)
@@ -298,7 +351,13 @@ def extra_forms(args):
     import paper_2211_16266_gb300 as pm
     forms, used = batched_forms(formats=("f16", "f32"), reps=3, tuning=BATCH_TUNING)
     runs = serving_runs(args.requests, [("served", "f16", pm.PMSP_SCHED_LANES), ("plain", "f32", None)])
+    prec = precision_forms()
     return dict(
+        precision=dict(metric="keyframes/s, 3840x1920, 8 views, 11x11/2, 8 iterations, best-3", unit="keyframes/s",
+                       value=prec["f16"]["keyframes_per_s"],
+                       config=dict(workload="one 3840x1920 keyframe, 8-bit texture + 2 DN noise, stored as fp32, "
+                                            "fp16 (centred) and uint8; FP32 arithmetic, FP64 poses"),
+                       forms=prec),
         batched=dict(metric=BATCHED_METRIC, unit="keyframes/s", value=forms["batched_f16"]["keyframes_per_s"],
                      config=dict(workload="32 mixed keyframes in one batch, CUDA graph, fp16 images", tuning=used),
                      forms=forms),
