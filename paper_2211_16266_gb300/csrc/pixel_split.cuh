@@ -337,7 +337,6 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
     static_assert(T == 2 || T == 4, "two or four warps per pixel group");
     using SM = TileSmemT<32, 8 / T, T>;
     constexpr int PIX = 128 / T;  // pixels of one colour per block
-    constexpr int GROUPS = 4 / T;
     __shared__ SM sm;
     __shared__ float xc[2][NS * PIX];  // view costs of the current candidate, double-buffered
     int tx, ty;
@@ -379,7 +378,6 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
         bn = make_float3(P.nx[i], P.ny[i], P.nz[i]);
         bc = P.cost[i];
     }
-    (void)GROUPS;
     const float span = P.inv_dmin - P.inv_dmax;
     const int n_cand = 8 + P.n_refine;
     int par = 0;
