@@ -1,9 +1,11 @@
 // C entry points over the serving runtime's GPU-free decisions
-// (paper_2211_16266_gb300/csrc/serving_policy.h), built by
-// tests/test_host_policy.py with the host compiler and called through ctypes.
+// (paper_2211_16266_gb300/csrc/serving_policy.h) and the tile order of the
+// launches and work lists (tile_order.h), built by tests/test_host_policy.py
+// with the host compiler and called through ctypes.
 #include <vector>
 
 #include "serving_policy.h"
+#include "tile_order.h"
 
 using namespace pmsp;
 
@@ -36,5 +38,7 @@ int sp_ring_pick_slot(const int* used, const int* loading, const int* pins, cons
     for (int i = 0; i < n; ++i) v[i] = SlotView{used[i] != 0, loading[i] != 0, pins[i], seq[i]};
     return ring_pick_slot(v.data(), n);
 }
+
+void sp_tile_of_block(int gx, int gy, int L, int* tx, int* ty) { tile_of_block(gx, gy, L, *tx, *ty); }
 
 }  // extern "C"

@@ -5,8 +5,10 @@ maps fit under the memory cap, the running tiles stay within the budget (a
 request alone always starts) and no running request shares a depth map with
 it in a way that needs ordering (both write one, or one writes what the
 other reads; reading the same neighbour is fine). A pushed frame takes a
-free slot, else evicts the oldest frame that no request holds. The policy
-header is built with the host compiler through a small ctypes shim.
+free slot, else evicts the oldest frame that no request holds. The tile order
+of the launches and of the batched and served work lists covers every tile of
+a grid exactly once. The headers are built with the host compiler through a
+small ctypes shim.
 """
 import ctypes
 import os
@@ -34,6 +36,8 @@ def lib(tmp_path_factory):
     L.sp_depth_conflict.argtypes = [ctypes.c_int, ip, ctypes.c_int, ip, ip, ip, ctypes.c_int]
     L.sp_admit_block.argtypes = [ctypes.c_int, ctypes.c_int, u64, u64, u64, u64, u64, u64, ctypes.c_int]
     L.sp_ring_pick_slot.argtypes = [ip, ip, ip, ctypes.POINTER(u64), ctypes.c_int]
+    L.sp_tile_of_block.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]
+    L.sp_tile_of_block.restype = None
     return L
 
 
@@ -160,3 +164,27 @@ def test_fifo_admission_simulated(lib):
             tiles_in_use += r["tiles"]
         assert queue == [] or running, "a queued request could never start"
     assert started == submitted
+
+
+def test_tile_order_is_a_bijection_in_strips(lib):
+    """Every launch and work list walks a gx x gy tile grid in strips of 8 tile rows,
+    column by column, and the rows below the last full strip row by row: each tile
+    exactly once (grids of 1..40 x 1..40 tiles and the 1920x960, 3840x1920 and 250x130
+    panoramas' grids of 32x8 tiles)."""
+    tx, ty = ctypes.c_int(), ctypes.c_int()
+    grids = [(gx, gy) for gx in range(1, 41) for gy in range(1, 41)]
+    grids += [(60, 120), (120, 240), (8, 17), ((250 + 31) // 32, (130 + 7) // 8)]
+    for gx, gy in grids:
+        seen = np.zeros((gy, gx), dtype=int)
+        order = []
+        for L in range(gx * gy):
+            lib.sp_tile_of_block(gx, gy, L, ctypes.byref(tx), ctypes.byref(ty))
+            assert 0 <= tx.value < gx and 0 <= ty.value < gy, (gx, gy, L)
+            seen[ty.value, tx.value] += 1
+            order.append((tx.value, ty.value))
+        assert np.all(seen == 1), (gx, gy)
+        # the first strip: 8 rows of column 0, then of column 1, ...
+        if gy >= 8:
+            assert order[:8] == [(0, r) for r in range(8)]
+            if gx > 1:
+                assert order[8] == (1, 0)
