@@ -267,7 +267,8 @@ def run_gpu(args):
                                units=dict(
                                    # one gather and four special-function results per view-sample
                                    gather_frac_of_l1_peak=achieved / peaks["gather_l1_per_s"],
-                                   sfu_frac=4 * achieved / peaks["sfu_per_s"]),
+                                   sfu_frac=4 * achieved / peaks["sfu_per_s"],
+                                   hbm=hbm_fraction(SWEEP_DRAM_BYTES, sweep_ms)),
                                measured_peaks=peaks)
         res["e2e"] = e2e
         gt = frames[KF].range
@@ -366,6 +367,21 @@ def extra_forms(args):
                      config=dict(workload=f"{args.requests} Poisson requests over a 64-frame fp16 ring, lanes "
                                           "scheduler, 40 GB admission cap"),
                      runs=runs))
+
+
+def hbm_fraction(bytes_per_launch, ms_per_launch):
+    """DRAM bytes of one half-sweep launch (ncu) over its duration, against the measured
+    copy bandwidth in MEASURED_PEAKS.json when it is there, else the 6.8 TB/s fallback."""
+    peak, basis = 6800.0, "fallback 6.8 TB/s"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, basis = float(json.load(f)["hbm_gbs"]), "measured copy bandwidth"
+    except (OSError, KeyError, ValueError):
+        pass
+    if bytes_per_launch is None:
+        return None
+    gbs = bytes_per_launch / (ms_per_launch / 1e3) / 1e9
+    return dict(achieved_gbs=gbs, peak_gbs=peak, frac=gbs / peak, peak_basis=basis)
 
 
 def time_sweeps(pm, ctx, stream, kf_args, params, out, flush):
