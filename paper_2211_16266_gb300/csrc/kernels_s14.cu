@@ -1,0 +1,6 @@
+// Instantiation of the per-pixel kernels for exactly 14 source views.
+#include "pixel_split.cuh"
+
+namespace pmsp {
+template cudaError_t launch_pixel_kernel_ns<14, true>(const PixelParams&, int, cudaStream_t);
+}  // namespace pmsp

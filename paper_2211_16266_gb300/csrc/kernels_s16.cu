@@ -1,6 +1,6 @@
-// Instantiation of the per-pixel kernels for 11 to 16 source views.
+// Instantiation of the per-pixel kernels for exactly 16 source views.
 #include "pixel_split.cuh"
 
 namespace pmsp {
-template cudaError_t launch_pixel_kernel_ns<16, false>(const PixelParams&, int, cudaStream_t);
+template cudaError_t launch_pixel_kernel_ns<16, true>(const PixelParams&, int, cudaStream_t);
 }  // namespace pmsp

@@ -80,6 +80,17 @@ constexpr int MAX_TILE_PITCH = 64 + 2 * MAX_HALO;
 // then transforms as R r = cl U_c - sl R_col1.
 constexpr int MAX_COL_PAIRS = 5;
 __shared__ float2 g_colU[MAX_COL_PAIRS][3][MAX_TILE_PITCH];
+// The same for 6 to 8 pairs (11 to 16 views), held only by the kernels of those
+// view counts, so the others keep their smaller shared-memory footprint.
+__shared__ float2 g_colU8[PMSP_MAX_SOURCES / 2][3][MAX_TILE_PITCH];
+
+template <int NP>
+__device__ __forceinline__ auto& col_table() {
+    if constexpr (NP <= MAX_COL_PAIRS)
+        return g_colU;
+    else
+        return g_colU8;
+}
 
 // Sample window of the paired cost loop: WIN 0 reads the window from the
 // parameters; the fixed windows make the loop bounds and offsets constants
@@ -454,9 +465,9 @@ __device__ __forceinline__ void pairs_sample(const PixelParams& P, float alpha, 
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         const auto VP = pair_of<VA>(P.pairs[q]);
-        const float2 Yx = fma2(av, g_colU[q][0][cx], fma2(bv, VP.r1(), VP.t0()));
-        const float2 Yy = fma2(av, g_colU[q][1][cx], fma2(bv, VP.r4(), VP.t1()));
-        const float2 Yz = fma2(av, g_colU[q][2][cx], fma2(bv, VP.r7(), VP.t2()));
+        const float2 Yx = fma2(av, col_table<NP>()[q][0][cx], fma2(bv, VP.r1(), VP.t0()));
+        const float2 Yy = fma2(av, col_table<NP>()[q][1][cx], fma2(bv, VP.r4(), VP.t1()));
+        const float2 Yz = fma2(av, col_table<NP>()[q][2][cx], fma2(bv, VP.r7(), VP.t2()));
         const float2 q2 = fma2(Yx, Yx, mul2(Yz, Yz));
         const float2 rho = make_float2(sqrt_approx(q2.x), sqrt_approx(q2.y));
         const float2 dl = add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y)));
@@ -644,15 +655,15 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, SM& sm, int b
     __syncthreads();
     if constexpr (EXACT && NS >= 2 && paired_views<VA>()) {
         constexpr int NP = NS / 2;
-        static_assert(NP <= MAX_COL_PAIRS, "column table too small");
+        static_assert(NP <= PMSP_MAX_SOURCES / 2, "column table too small");
         const int cols = SM::W + 2 * P.radius;
         for (int i = threadIdx.x; i < cols * NP; i += BLOCK_THREADS) {
             const int q = i / cols, c = i - q * cols;
             const PixelParams::ViewPair& VP = P.pairs[q];
             const float2 sn = pair(sm.col_sin[c]), cs = pair(sm.col_cos[c]);
-            g_colU[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
-            g_colU[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
-            g_colU[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
+            col_table<NP>()[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
+            col_table<NP>()[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
+            col_table<NP>()[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
         }
         __syncthreads();
     }
@@ -782,7 +793,7 @@ cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t 
         case MODE_INIT: pixel_kernel<NS, EXACT, MODE_INIT><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
         default:
             // views split over several warps per pixel (a tuning choice; same maps)
-            if constexpr (NS >= 2)
+            if constexpr (EXACT && NS >= 2)
                 if (p.tpp > 1) return launch_split_sweep<NS, EXACT>(p, stream);
             // the half-sweep dominates the run time: fixed-window instances for the
             // paired path (exact view counts of at least 2), in three tile shapes

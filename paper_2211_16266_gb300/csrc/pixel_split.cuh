@@ -1,8 +1,8 @@
 // Half-sweep with several threads per pixel: the views of one pixel are split
 // over T warps (T = 2 or 4). The T warps of a pixel group hold the same 32
 // pixels, one per lane; warp `sub` of the group evaluates the view pairs
-// q = sub, sub + T, ... (or, for the guarded view count, the views
-// s = sub, sub + T, ...). Each warp writes its views' costs of the current
+// q = sub, sub + T, ... (and the odd last view in one of them). Each warp
+// writes its views' costs of the current
 // candidate to shared memory, the group meets at a named barrier, and every
 // warp then reads all view costs of its pixel, sorts them and averages the
 // best k itself, so all T warps take the same decision. The split lowers the
@@ -48,9 +48,9 @@ __device__ __forceinline__ void pairs_sample_sub(const PixelParams& P, float alp
     for (int j = 0; j < NPL; ++j) {
         const int q = SUB + j * T;
         const PixelParams::ViewPair& VP = P.pairs[q];
-        const float2 Yx = fma2(av, g_colU[q][0][cx], fma2(bv, VP.R[1], VP.t[0]));
-        const float2 Yy = fma2(av, g_colU[q][1][cx], fma2(bv, VP.R[4], VP.t[1]));
-        const float2 Yz = fma2(av, g_colU[q][2][cx], fma2(bv, VP.R[7], VP.t[2]));
+        const float2 Yx = fma2(av, col_table<NP>()[q][0][cx], fma2(bv, VP.R[1], VP.t[0]));
+        const float2 Yy = fma2(av, col_table<NP>()[q][1][cx], fma2(bv, VP.R[4], VP.t[1]));
+        const float2 Yz = fma2(av, col_table<NP>()[q][2][cx], fma2(bv, VP.R[7], VP.t[2]));
         const float2 q2 = fma2(Yx, Yx, mul2(Yz, Yz));
         const float2 rho = make_float2(sqrt_approx(q2.x), sqrt_approx(q2.y));
         const float2 dl = add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y)));
@@ -189,122 +189,17 @@ __device__ __forceinline__ void pair_costs_sub(const PixelParams& P, const SM& s
     if (MY_ODD) xc[(NS - 1) * pix_stride + pix] = view_cost(SJo, SJJo, SIJo);
 }
 
-// Per-view costs of views s = SUB, SUB + T, ... < S (the guarded view count),
-// with the arithmetic of plane_cost.
-template <int NS, int T, int SUB, class SM>
-__device__ __forceinline__ void guarded_costs_sub(const PixelParams& P, const SM& sm, int lx, int ly,
-                                                  const RefStats& st, float3 rp, float d, float3 n, float* xc, int pix,
-                                                  int pix_stride) {
-    constexpr int NL = (NS - SUB + T - 1) / T;
-    const float eps = 1e-8f * st.Sw * st.Sw;
-    auto store_all = [&](float c) {
-#pragma unroll
-        for (int j = 0; j < NL; ++j) xc[(SUB + j * T) * pix_stride + pix] = c;
-    };
-    if (st.varI < eps) {
-        store_all(2.0f);
-        return;
-    }
-    const float dn = d * (n.x * rp.x + n.y * rp.y + n.z * rp.z);
-    const int K = P.K, R = P.radius, stp = P.stride;
-    const int ac = K >> 1;
-    float c0[NL], SJ[NL], SJJ[NL], SIJ[NL];
-    {
-        const int o = ac * stp - R;
-        const float cl = sm.row_cos[ly + o];
-        const float3 rq = make_float3(cl * sm.col_sin[lx + o], -sm.row_sin[ly + o], cl * sm.col_cos[lx + o]);
-        const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
-        if (!(den < -1e-6f)) {
-            store_all(2.0f);
-            return;
-        }
-        const float t = __fdividef(dn, den);
-        const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
-#pragma unroll
-        for (int j = 0; j < NL; ++j) {
-            const int s = SUB + j * T;
-            c0[j] = 0.f;
-            SJ[j] = 0.f;
-            SJJ[j] = 0.f;
-            SIJ[j] = 0.f;
-            if (s < P.S) c0[j] = view_sample<ParamViews>(P.src[s], X, Y, Z);
-        }
-    }
-    bool valid = true;
-    for (int a = 0; a < K && valid; ++a) {
-        const int oy = a * stp - R;
-        const float cl = sm.row_cos[ly + oy], msl = -sm.row_sin[ly + oy];
-        const float* ref_row = sm.ref + (ly + oy) * SM::PITCH + lx - R;
-        for (int b = 0; b < K; ++b) {
-            if (a == ac && b == ac) continue;
-            const float Iq = ref_row[b * stp];
-            const float w = bilateral(P, sm, a, b, Iq, st.Ip);
-            const float wI = w * (Iq - st.mu);
-            const int cx = lx + b * stp - R;
-            const float3 rq = make_float3(cl * sm.col_sin[cx], msl, cl * sm.col_cos[cx]);
-            const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
-            if (!(den < -1e-6f)) {
-                valid = false;
-                break;
-            }
-            const float t = __fdividef(dn, den);
-            const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
-#pragma unroll
-            for (int j = 0; j < NL; ++j) {
-                const int s = SUB + j * T;
-                if (s < P.S) {
-                    const float Jc = view_sample<ParamViews>(P.src[s], X, Y, Z) - c0[j];
-                    const float tw = w * Jc;
-                    SJ[j] += tw;
-                    SJJ[j] = fmaf(tw, Jc, SJJ[j]);
-                    SIJ[j] = fmaf(wI, Jc, SIJ[j]);
-                }
-            }
-        }
-    }
-    if (!valid) {
-        store_all(2.0f);
-        return;
-    }
-#pragma unroll
-    for (int j = 0; j < NL; ++j) {
-        const int s = SUB + j * T;
-        float c = 3.0f;  // unused slots sort last
-        if (s < P.S) {
-            const float varJ = st.Sw * SJJ[j] - SJ[j] * SJ[j];
-            const float cov = st.Sw * SIJ[j] - st.SIc * SJ[j];
-            if (varJ < eps) {
-                c = 2.0f;
-            } else {
-                float ncc = cov * rsqrtf(st.varI * varJ);
-                ncc = fminf(1.0f, fmaxf(-1.0f, ncc));
-                c = 1.0f - ncc;
-            }
-        }
-        xc[s * pix_stride + pix] = c;
-    }
-}
-
 // This warp's share of the view costs: a warp-uniform switch over the warp's
-// index in its group, so every view or pair index is a compile-time constant.
-template <int NS, bool EXACT, int T, int WIN, class SM>
+// index in its group, so every pair index is a compile-time constant.
+template <int NS, int T, int WIN, class SM>
 __device__ __forceinline__ void view_costs_split(int sub, const PixelParams& P, const SM& sm, int lx, int ly,
                                                  const RefStats& st, float3 rp, float d, float3 n, float* xc, int pix,
                                                  int pix_stride) {
-    if constexpr (EXACT && NS >= 2) {
-        switch (sub) {
-            case 0: pair_costs_sub<NS, T, 0, WIN>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
-            case 1: pair_costs_sub<NS, T, 1, WIN>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
-            case 2: if constexpr (T > 2) pair_costs_sub<NS, T, 2, WIN>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
-            default: if constexpr (T > 3) pair_costs_sub<NS, T, 3, WIN>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
-        }
-    } else {
-        switch (sub) {
-            case 0: guarded_costs_sub<NS, T, 0>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
-            case 1: guarded_costs_sub<NS, T, 1>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
-            case 2: if constexpr (T > 2) guarded_costs_sub<NS, T, 2>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
-            default: if constexpr (T > 3) guarded_costs_sub<NS, T, 3>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
-        }
+    switch (sub) {
+        case 0: pair_costs_sub<NS, T, 0, WIN>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
+        case 1: pair_costs_sub<NS, T, 1, WIN>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
+        case 2: if constexpr (T > 2) pair_costs_sub<NS, T, 2, WIN>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
+        default: if constexpr (T > 3) pair_costs_sub<NS, T, 3, WIN>(P, sm, lx, ly, st, rp, d, n, xc, pix, pix_stride); break;
     }
 }
 
@@ -331,10 +226,11 @@ __device__ __forceinline__ float best_k_mean(const PixelParams& P, const float* 
     return sum / (float)P.best_k;
 }
 
-template <int NS, bool EXACT, int T, int WIN>
+template <int NS, int T, int WIN>
 __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
     pixel_split_kernel(const __grid_constant__ PixelParams P) {
     static_assert(T == 2 || T == 4, "two or four warps per pixel group");
+    static_assert(NS >= 2, "view pairs");
     using SM = TileSmemT<32, 8 / T, T>;
     constexpr int PIX = 128 / T;  // pixels of one colour per block
     __shared__ SM sm;
@@ -344,16 +240,16 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
     const int bx = tx * SM::W, by = ty * SM::H;
     stage_tile(P, sm, bx, by);
     __syncthreads();
-    if constexpr (EXACT && NS >= 2) {
+    {
         constexpr int NP = NS / 2;
         const int cols = SM::W + 2 * P.radius;
         for (int i = threadIdx.x; i < cols * NP; i += BLOCK_THREADS) {
             const int q = i / cols, c = i - q * cols;
             const PixelParams::ViewPair& VP = P.pairs[q];
             const float2 sn = pair(sm.col_sin[c]), cs = pair(sm.col_cos[c]);
-            g_colU[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
-            g_colU[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
-            g_colU[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
+            col_table<NP>()[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
+            col_table<NP>()[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
+            col_table<NP>()[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
         }
         __syncthreads();
     }
@@ -410,7 +306,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
             const float il = 1.0f / sqrtf(nc.x * nc.x + nc.y * nc.y + nc.z * nc.z);
             nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
         }
-        if (ok) view_costs_split<NS, EXACT, T, WIN>(sub, P, sm, lx, ly, st, rp, dc, nc, xc[par], pix, PIX);
+        if (ok) view_costs_split<NS, T, WIN>(sub, P, sm, lx, ly, st, rp, dc, nc, xc[par], pix, PIX);
         group_barrier<T>(group);
         if (ok) {
             const float c = best_k_mean<NS>(P, xc[par], pix, PIX);
@@ -431,20 +327,20 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
     }
 }
 
-template <int NS, bool EXACT, int T>
+template <int NS, int T>
 inline cudaError_t launch_split_sweep_t(const PixelParams& p, cudaStream_t stream) {
     const dim3 grid((p.W + 31) / 32, (p.H + 8 / T - 1) / (8 / T));
-    const int win = (EXACT && NS >= 2) ? window_of(p) : 0;
-    if (win == 1)
-        pixel_split_kernel<NS, EXACT, T, 1><<<grid, BLOCK_THREADS, 0, stream>>>(p);
+    if (window_of(p) == 1)
+        pixel_split_kernel<NS, T, 1><<<grid, BLOCK_THREADS, 0, stream>>>(p);
     else
-        pixel_split_kernel<NS, EXACT, T, 0><<<grid, BLOCK_THREADS, 0, stream>>>(p);
+        pixel_split_kernel<NS, T, 0><<<grid, BLOCK_THREADS, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
 template <int NS, bool EXACT>
 cudaError_t launch_split_sweep(const PixelParams& p, cudaStream_t stream) {
-    return p.tpp >= 4 ? launch_split_sweep_t<NS, EXACT, 4>(p, stream) : launch_split_sweep_t<NS, EXACT, 2>(p, stream);
+    static_assert(EXACT, "the split half-sweep serves exact view counts");
+    return p.tpp >= 4 ? launch_split_sweep_t<NS, 4>(p, stream) : launch_split_sweep_t<NS, 2>(p, stream);
 }
 
 }  // namespace pmsp

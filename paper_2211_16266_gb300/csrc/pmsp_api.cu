@@ -22,8 +22,8 @@ namespace pmsp {
 template <int NS, bool EXACT>
 cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t stream);
 
-// One instantiation per source count 1..10 (views unrolled without guards),
-// a guarded 16-view one above.
+// One instantiation per source count 1..16 (views unrolled without guards,
+// in packed pairs from 2 views on).
 cudaError_t launch_pixel_kernel(const PixelParams& p, int mode, cudaStream_t stream) {
     switch (p.S) {
         case 1: return launch_pixel_kernel_ns<1, true>(p, mode, stream);
@@ -36,7 +36,12 @@ cudaError_t launch_pixel_kernel(const PixelParams& p, int mode, cudaStream_t str
         case 8: return launch_pixel_kernel_ns<8, true>(p, mode, stream);
         case 9: return launch_pixel_kernel_ns<9, true>(p, mode, stream);
         case 10: return launch_pixel_kernel_ns<10, true>(p, mode, stream);
-        default: return launch_pixel_kernel_ns<16, false>(p, mode, stream);
+        case 11: return launch_pixel_kernel_ns<11, true>(p, mode, stream);
+        case 12: return launch_pixel_kernel_ns<12, true>(p, mode, stream);
+        case 13: return launch_pixel_kernel_ns<13, true>(p, mode, stream);
+        case 14: return launch_pixel_kernel_ns<14, true>(p, mode, stream);
+        case 15: return launch_pixel_kernel_ns<15, true>(p, mode, stream);
+        default: return launch_pixel_kernel_ns<16, true>(p, mode, stream);
     }
 }
 

@@ -81,9 +81,10 @@ def test_batch_equals_single_keyframe_runs(pm, ctx):
 
 def test_batch_with_more_than_ten_sources(pm, ctx):
     """A batch whose largest view count is above 10 runs the guarded 16-view
-    instance of the persistent kernel (and of the per-keyframe chains): it
-    matches the single-keyframe runs within the parity tolerance, and the chains
-    bit for bit."""
+    instance of the persistent kernel (per-view arithmetic, views in shared
+    memory): it matches the single-keyframe runs (exact 12- and 4-view kernels)
+    within the parity tolerance; the per-keyframe chains run those kernels and
+    match bit for bit."""
     pa = scenes.trajectory_problem(96, 48, 12, seed_scene=1014)
     pa.params = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=2, best_k=4, sigma_color=0.2,
                      sigma_space=3.0, n_refine=6, neighbor_table=0, seed=3, keyframe_id=21)
@@ -187,8 +188,8 @@ def test_threads_per_pixel_match_the_oracle(pm, ctx, tpp):
     bit for bit (same sums in the same order, same sort), and the FP64 oracle's
     whole densification within the bar (cost 1e-4, range 0.5 % on 99.5 % of
     pixels). Problems: 6 views (3 pairs: uneven over 2 warps, one warp idle at
-    4), 7 views in fp16 (an odd view), 12 views (the guarded path), ragged
-    tiles."""
+    4), 7 views in fp16 (an odd view), 12 views (6 pairs: 3 per warp at 2,
+    uneven at 4), ragged tiles."""
     p1 = scenes.config1(W=384, H=192)
     p2 = scenes.trajectory_problem(250, 130, 7, seed_scene=1016, fmt="f16")
     p2.params = dict(p1.params, iterations=3, best_k=2, keyframe_id=41)

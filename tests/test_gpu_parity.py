@@ -60,7 +60,7 @@ def _problem(name):
         p2.params = p.params
         return p2
     if name == "max16":
-        # the largest view count and window: 16 sources (the guarded 16-view kernel),
+        # the largest view count and window: 16 sources (8 view pairs, the 8-pair column table),
         # 21x21 window sampled densely (441 samples, rows clamped at both poles),
         # best-k = S, on a panorama of ragged tiles
         p = scenes.trajectory_problem(48, 24, 16, seed_scene=1013)
