@@ -88,6 +88,16 @@ def test_create_without_a_gpu_reports_a_cuda_error(lib):
     assert h.value is None
 
 
+def test_create_refuses_an_unknown_scheduler(lib):
+    """The serving scheduler is checked before any CUDA call: an unknown value is
+    PMSP_EINVAL on any machine, and the handle stays NULL."""
+    for bad in (2, -1, 7):
+        h = ctypes.c_void_p(1)
+        opts = lib.pmsp_ctx_opts(0, None, 0, 0, 0, bad)
+        assert lib._lib.pmsp_create(ctypes.byref(h), ctypes.byref(opts)) == lib.PMSP_EINVAL
+        assert h.value is None
+
+
 STRUCTS = ("pmsp_image", "pmsp_pose", "pmsp_params", "pmsp_maps", "pmsp_ctx_opts", "pmsp_batch_item",
            "pmsp_tuning", "pmsp_request", "pmsp_serving_stats", "pmsp_peaks")
 
@@ -123,7 +133,8 @@ def test_binding_constants_match_the_header(lib, tmp_path):
     import subprocess
     names = {n: n for n in ("PMSP_OK", "PMSP_EINVAL", "PMSP_ENOMEM", "PMSP_EADMIT", "PMSP_EBUSY", "PMSP_ETIMEDOUT",
                             "PMSP_ECUDA", "PMSP_EDEVICE", "PMSP_ENOTFOUND", "PMSP_U8", "PMSP_F16", "PMSP_F32",
-                            "PMSP_HOST", "PMSP_DEVICE", "PMSP_BATCH_GRAPH", "PMSP_NOALLOC_MAX_ITEMS")}
+                            "PMSP_HOST", "PMSP_DEVICE", "PMSP_BATCH_GRAPH", "PMSP_NOALLOC_MAX_ITEMS",
+                            "PMSP_SCHED_LANES", "PMSP_SCHED_STEPS")}
     names["MAX_SOURCES"] = "PMSP_MAX_SOURCES"
     lines = ['#include <stdio.h>', '#include "pmsp.h"', 'int main(void) {']
     lines += [f'    printf("{py} %lld\\n", (long long)({c}));' for py, c in names.items()]

@@ -210,3 +210,16 @@ def test_threads_per_pixel_match_the_oracle(pm, ctx, tpp):
         gd, gc = gd.astype(np.float64), gc.astype(np.float64)
         assert np.mean(np.abs(gd - od) / od <= 5e-3) >= 0.995
         assert np.mean(np.abs(gc - oc) <= 1e-4) >= 0.995
+
+
+def test_invalid_tuning_is_refused(pm, ctx):
+    """Threads per pixel other than 0, 1, 2 or 4 and tile shapes outside 0..2 are
+    refused with PMSP_EINVAL before anything runs; the context stays usable."""
+    p = scenes.config0(W=64, H=32)
+    args = _args(p)
+    for bad in (pm.pmsp_tuning(0, 0, 0, 1, 0, 3), pm.pmsp_tuning(0, 0, 0, 1, 0, 8), pm.pmsp_tuning(0, 0, 0, 1, 3, 1)):
+        with pytest.raises(pm.PmspError) as e:
+            pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=bad)
+        assert e.value.code == pm.PMSP_EINVAL
+    pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=pm.pmsp_tuning(0, 0, 0, 1, 0, 2))
+    pm.pmsp_sync(ctx)
