@@ -345,28 +345,44 @@ BATCH_TUNING = (0, 0, 0, 1, 0, 1)
 
 
 def extra_forms(args):
-    """The batched and served forms beside the keyframe line (N = 1 only): the 32-keyframe
-    batch in fp16 against the plain per-keyframe path with fp32 images, and the served
-    fp16 ring (lanes) against the plain fp32 FIFO on the Poisson trace, with ground-truth
-    accuracy and latency."""
+    """The batched, served and precision forms beside the keyframe line (N = 1 only): the
+    32-keyframe batch in fp16 against the plain per-keyframe path with fp32 images, the
+    served fp16 ring (lanes) against the plain fp32 FIFO on the Poisson trace, and one
+    3840x1920 keyframe stored three ways, with ground-truth accuracy and latency. A form
+    that fails reports its error in its own key; the keyframe line is printed either way."""
+    import traceback
     import paper_2211_16266_gb300 as pm
-    forms, used = batched_forms(formats=("f16", "f32"), reps=3, tuning=BATCH_TUNING)
-    runs = serving_runs(args.requests, [("served", "f16", pm.PMSP_SCHED_LANES), ("plain", "f32", None)])
-    prec = precision_forms()
-    return dict(
-        precision=dict(metric="keyframes/s, 3840x1920, 8 views, 11x11/2, 8 iterations, best-3", unit="keyframes/s",
-                       value=prec["f16"]["keyframes_per_s"],
-                       config=dict(workload="one 3840x1920 keyframe, 8-bit texture + 2 DN noise, stored as fp32, "
-                                            "fp16 (centred) and uint8; FP32 arithmetic, FP64 poses"),
-                       forms=prec),
-        batched=dict(metric=BATCHED_METRIC, unit="keyframes/s", value=forms["batched_f16"]["keyframes_per_s"],
-                     config=dict(workload="32 mixed keyframes in one batch, CUDA graph, fp16 images", tuning=used),
-                     forms=forms),
-        serving=dict(metric=SERVING_METRIC, unit="keyframes/s", value=runs["served_f16_lanes"]["keyframes_per_s"],
-                     latency_ms=dict(p50=runs["served_f16_lanes"]["p50_ms"], p99=runs["served_f16_lanes"]["p99_ms"]),
-                     config=dict(workload=f"{args.requests} Poisson requests over a 64-frame fp16 ring, lanes "
-                                          "scheduler, 40 GB admission cap"),
-                     runs=runs))
+
+    def guarded(fn):
+        try:
+            return fn()
+        except Exception as e:  # keep the headline line: report the failure in the extra's key
+            traceback.print_exc(file=sys.stderr)
+            return dict(error=f"{type(e).__name__}: {e}")
+
+    def batched():
+        forms, used = batched_forms(formats=("f16", "f32"), reps=3, tuning=BATCH_TUNING)
+        return dict(metric=BATCHED_METRIC, unit="keyframes/s", value=forms["batched_f16"]["keyframes_per_s"],
+                    config=dict(workload="32 mixed keyframes in one batch, CUDA graph, fp16 images", tuning=used),
+                    forms=forms)
+
+    def serving():
+        runs = serving_runs(args.requests, [("served", "f16", pm.PMSP_SCHED_LANES), ("plain", "f32", None)])
+        return dict(metric=SERVING_METRIC, unit="keyframes/s", value=runs["served_f16_lanes"]["keyframes_per_s"],
+                    latency_ms=dict(p50=runs["served_f16_lanes"]["p50_ms"], p99=runs["served_f16_lanes"]["p99_ms"]),
+                    config=dict(workload=f"{args.requests} Poisson requests over a 64-frame fp16 ring, lanes "
+                                         "scheduler, 40 GB admission cap"),
+                    runs=runs)
+
+    def precision():
+        prec = precision_forms()
+        return dict(metric="keyframes/s, 3840x1920, 8 views, 11x11/2, 8 iterations, best-3", unit="keyframes/s",
+                    value=prec["f16"]["keyframes_per_s"],
+                    config=dict(workload="one 3840x1920 keyframe, 8-bit texture + 2 DN noise, stored as fp32, "
+                                         "fp16 (centred) and uint8; FP32 arithmetic, FP64 poses"),
+                    forms=prec)
+
+    return dict(batched=guarded(batched), serving=guarded(serving), precision=guarded(precision))
 
 
 def hbm_fraction(bytes_per_launch, ms_per_launch):
