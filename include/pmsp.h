@@ -394,9 +394,10 @@ typedef struct {
                               (every shape computes the same numbers) */
     int32_t tpp;           /* strategy 1, half-sweeps of keyframes with 2 or more sources:
                               threads per pixel, 0 or 1: one; 2 or 4: the pixel's view pairs
-                              (views, above 10 sources) split over 2 or 4 warps that exchange
-                              their view costs through shared memory; the same numbers, fewer
-                              registers per thread (tile 32x4 or 32x2, `tile` ignored) */
+                              split over 2 or 4 warps that exchange their view costs through
+                              shared memory; the same numbers, fewer registers per thread
+                              (tile 32x4 or 32x2, `tile` ignored); 0, 1, 2 or 4, else
+                              PMSP_EINVAL */
 } pmsp_tuning;
 
 #define PMSP_BATCH_GRAPH 1u /* capture the batch in a CUDA graph and replay it when the identical
