@@ -47,10 +47,11 @@ constexpr int MAX_K = 2 * MAX_HALO + 1;
 constexpr int min_blocks_for(int ns) { return ns <= 4 ? 8 : ns <= 6 ? 7 : ns <= 8 ? 6 : ns <= 10 ? 5 : 4; }
 
 // Resident blocks per SM of the single-keyframe kernels, by view count:
-// 72 registers up to 6 views (7 blocks; 2.5 % faster than the 6-view sweep's
-// own 80), 96 for 7-8 views and 128 beyond (no spills; the compiler left
-// alone takes up to 246). Measured on 1920x960 half-sweeps.
-constexpr int pixel_min_blocks(int ns) { return ns <= 6 ? 7 : ns <= 8 ? 5 : 4; }
+// 5 (96 registers) up to 4 views, 4 (128) for 5-8 views, 3 (168) for 9-10
+// and 4 beyond (the compiler left alone takes up to 246). Each tier is the
+// fastest of 3-7 blocks on 1920x960 half-sweeps: fewer, spill-free threads
+// beat more resident warps once the per-view sums fill the registers.
+constexpr int pixel_min_blocks(int ns) { return ns <= 4 ? 5 : ns <= 8 ? 4 : ns <= 10 ? 3 : 4; }
 
 // Shared memory of one tile of TW x TH reference pixels (halo included);
 // every shape has (TW / 2) x TH pixels of one colour and TPP threads per

@@ -24,8 +24,11 @@
 namespace pmsp {
 
 // Resident blocks the split kernels' register budget is sized for: a warp
-// keeps about NS / T views' sums.
-constexpr int split_min_blocks(int ns, int t) { return pixel_min_blocks((ns + t - 1) / t) + (t > 1 ? 1 : 0); }
+// keeps about NS / T views' sums, so the budget follows the views per warp
+// (8 blocks up to 6, 6 up to 8, 5 beyond).
+constexpr int split_min_blocks(int ns, int t) {
+    return t == 1 ? pixel_min_blocks(ns) : (ns + t - 1) / t <= 6 ? 8 : (ns + t - 1) / t <= 8 ? 6 : 5;
+}
 
 // Barrier of pixel group `group` (its T warps); ids 1 and 2 as constants, so
 // the kernel reserves two named barriers besides __syncthreads'.
