@@ -38,9 +38,6 @@ static __constant__ int c_neighbors[2][8][2] = {
     {{0, -3}, {0, 3}, {-3, 0}, {3, 0}, {0, -5}, {0, 5}, {-5, 0}, {5, 0}},
     {{0, -1}, {0, 1}, {-1, 0}, {1, 0}, {0, -5}, {0, 5}, {-5, 0}, {5, 0}}};
 
-constexpr int TILE_PITCH = TILE_W + 2 * MAX_HALO;
-constexpr int TILE_ROWS = TILE_H + 2 * MAX_HALO;
-constexpr int MAX_K = 2 * MAX_HALO + 1;
 
 // Resident blocks per SM the batched kernel's register budget is sized for,
 // by its largest view count (its per-view-count variants share one budget).
@@ -53,44 +50,47 @@ constexpr int min_blocks_for(int ns) { return ns <= 4 ? 8 : ns <= 6 ? 7 : ns <= 
 // beat more resident warps once the per-view sums fill the registers.
 constexpr int pixel_min_blocks(int ns) { return ns <= 4 ? 5 : ns <= 8 ? 4 : ns <= 10 ? 3 : 4; }
 
-// Shared memory of one tile of TW x TH reference pixels (halo included);
-// every shape has (TW / 2) x TH pixels of one colour and TPP threads per
-// pixel, 128 threads in all.
-template <int TW, int TH, int TPP = 1>
+// Shared memory of one tile of TW x TH reference pixels with a halo of HALO
+// pixels on each side (the window radius the tile serves: the largest, or
+// that of a fixed-window instance); every shape has (TW / 2) x TH pixels of
+// one colour and TPP threads per pixel, 128 threads in all.
+template <int TW, int TH, int TPP = 1, int HALO = MAX_HALO>
 struct TileSmemT {
     static constexpr int W = TW, H = TH;
-    static constexpr int PITCH = TW + 2 * MAX_HALO, ROWS = TH + 2 * MAX_HALO;
+    static constexpr int PITCH = TW + 2 * HALO, ROWS = TH + 2 * HALO;
     static constexpr int THREADS = (TW / 2) * TH;
     static_assert(THREADS * TPP == BLOCK_THREADS, "every tile shape runs 128 threads");
+    static_assert(HALO >= 0 && HALO <= MAX_HALO, "halo within the largest window");
     float ref[ROWS * PITCH];             // normalised intensities, halo included
     float row_cos[ROWS], row_sin[ROWS];  // cos lat, sin lat
     float col_sin[PITCH], col_cos[PITCH];  // sin lon, cos lon
-    float wsp[MAX_K];                    // spatial log2-weight of offset index k
+    float wsp[2 * HALO + 1];             // spatial log2-weight of offset index k
 };
 using TileSmem = TileSmemT<TILE_W, TILE_H>;  // the batched and no-alloc kernels' shape
 
 // Tile shapes of the single-keyframe half-sweep, chosen by PixelParams::tile.
-template <int TS> struct TileShape { using Smem = TileSmemT<32, 8>; };
-template <> struct TileShape<1> { using Smem = TileSmemT<64, 4>; };
-template <> struct TileShape<2> { using Smem = TileSmemT<16, 16>; };
-constexpr int MAX_TILE_PITCH = 64 + 2 * MAX_HALO;
+template <int TS, int HALO = MAX_HALO> struct TileShape { using Smem = TileSmemT<32, 8, 1, HALO>; };
+template <int HALO> struct TileShape<1, HALO> { using Smem = TileSmemT<64, 4, 1, HALO>; };
+template <int HALO> struct TileShape<2, HALO> { using Smem = TileSmemT<16, 16, 1, HALO>; };
 
 // Rotated column directions of the paired path: for view pair q and tile
 // column c, colU[q][k][c] = row k of R_s applied to (sin lon_c, 0, cos lon_c)
 // for both views of the pair. A sample direction r = (cl sin, -sl, cl cos)
-// then transforms as R r = cl U_c - sl R_col1.
+// then transforms as R r = cl U_c - sl R_col1. One table per kernel, sized
+// by the tile's columns (PITCH, halo included) and by CAP pairs: 5 for up to
+// 10 views, so the batched kernel's view counts share one table, and 8 only
+// in the kernels of 11 to 16 views.
 constexpr int MAX_COL_PAIRS = 5;
-__shared__ float2 g_colU[MAX_COL_PAIRS][3][MAX_TILE_PITCH];
-// The same for 6 to 8 pairs (11 to 16 views), held only by the kernels of those
-// view counts, so the others keep their smaller shared-memory footprint.
-__shared__ float2 g_colU8[PMSP_MAX_SOURCES / 2][3][MAX_TILE_PITCH];
 
-template <int NP>
+template <int CAP, int PITCH>
+__device__ __forceinline__ auto& col_array() {
+    __shared__ float2 t[CAP][3][PITCH];
+    return t;
+}
+
+template <int NP, int PITCH>
 __device__ __forceinline__ auto& col_table() {
-    if constexpr (NP <= MAX_COL_PAIRS)
-        return g_colU;
-    else
-        return g_colU8;
+    return col_array<NP <= MAX_COL_PAIRS ? MAX_COL_PAIRS : PMSP_MAX_SOURCES / 2, PITCH>();
 }
 
 // Sample window of the paired cost loop: WIN 0 reads the window from the
@@ -99,18 +99,21 @@ __device__ __forceinline__ auto& col_table() {
 // (6 x 6 samples, radius 5); WIN 2: 7x7 dense (7 x 7, radius 3).
 template <int WIN>
 struct Window {
+    static constexpr int HALO = MAX_HALO;  // the tile halo the instance needs
     __device__ static int K(const PixelParams& P) { return P.K; }
     __device__ static int R(const PixelParams& P) { return P.radius; }
     __device__ static int stride(const PixelParams& P) { return P.stride; }
 };
 template <>
 struct Window<1> {
+    static constexpr int HALO = 5;
     __device__ static constexpr int K(const PixelParams&) { return 6; }
     __device__ static constexpr int R(const PixelParams&) { return 5; }
     __device__ static constexpr int stride(const PixelParams&) { return 2; }
 };
 template <>
 struct Window<2> {
+    static constexpr int HALO = 3;
     __device__ static constexpr int K(const PixelParams&) { return 7; }
     __device__ static constexpr int R(const PixelParams&) { return 3; }
     __device__ static constexpr int stride(const PixelParams&) { return 1; }
@@ -458,7 +461,7 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const SM& sm, 
 // gathers are in flight while the next pairs' coordinates are computed; then
 // the interpolation of every pair (2 % faster than pair by pair, and issuing
 // each pair's gathers before the next pair's coordinates another 1.5 %).
-template <int NP, class VA>
+template <int NP, class VA, int PITCH>
 __device__ __forceinline__ void pairs_sample(const PixelParams& P, float alpha, float beta, int cx, float2 (&J)[NP]) {
     float2 fx[NP], fy[NP];
     float4 G0[NP], G1[NP];
@@ -466,9 +469,9 @@ __device__ __forceinline__ void pairs_sample(const PixelParams& P, float alpha, 
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         const auto VP = pair_of<VA>(P.pairs[q]);
-        const float2 Yx = fma2(av, col_table<NP>()[q][0][cx], fma2(bv, VP.r1(), VP.t0()));
-        const float2 Yy = fma2(av, col_table<NP>()[q][1][cx], fma2(bv, VP.r4(), VP.t1()));
-        const float2 Yz = fma2(av, col_table<NP>()[q][2][cx], fma2(bv, VP.r7(), VP.t2()));
+        const float2 Yx = fma2(av, col_table<NP, PITCH>()[q][0][cx], fma2(bv, VP.r1(), VP.t0()));
+        const float2 Yy = fma2(av, col_table<NP, PITCH>()[q][1][cx], fma2(bv, VP.r4(), VP.t1()));
+        const float2 Yz = fma2(av, col_table<NP, PITCH>()[q][2][cx], fma2(bv, VP.r7(), VP.t2()));
         const float2 q2 = fma2(Yx, Yx, mul2(Yz, Yz));
         const float2 rho = make_float2(sqrt_approx(q2.x), sqrt_approx(q2.y));
         const float2 dl = add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y)));
@@ -525,7 +528,7 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
         const float t = __fdividef(dn, den);
         const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
         const float alpha = t * cl, beta = -t * sm.row_sin[ly + o];
-        pairs_sample<NP, VA>(P, alpha, beta, lx + o, c0);
+        pairs_sample<NP, VA, SM::PITCH>(P, alpha, beta, lx + o, c0);
 #pragma unroll
         for (int q = 0; q < NP; ++q) SJ[q] = SJJ[q] = SIJ[q] = pair(0.f);
         if (ODD) c0o = view_sample<VA>(P.src[NS - 1], X, Y, Z);
@@ -553,7 +556,7 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
             const float alpha = t * cl, beta = t * msl;
             const float2 w2 = pair(w), wI2 = pair(wI);
             float2 Jall[NP];
-            pairs_sample<NP, VA>(P, alpha, beta, cx, Jall);
+            pairs_sample<NP, VA, SM::PITCH>(P, alpha, beta, cx, Jall);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const float2 J = Jall[q];
@@ -662,9 +665,9 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, SM& sm, int b
             const int q = i / cols, c = i - q * cols;
             const PixelParams::ViewPair& VP = P.pairs[q];
             const float2 sn = pair(sm.col_sin[c]), cs = pair(sm.col_cos[c]);
-            col_table<NP>()[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
-            col_table<NP>()[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
-            col_table<NP>()[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
+            col_table<NP, SM::PITCH>()[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
+            col_table<NP, SM::PITCH>()[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
+            col_table<NP, SM::PITCH>()[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
         }
         __syncthreads();
     }
@@ -751,7 +754,7 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, SM& sm, int b
 
 template <int NS, bool EXACT, int MODE, int WIN = 0, int TS = 0>
 __global__ void __launch_bounds__(BLOCK_THREADS, pixel_min_blocks(NS)) pixel_kernel(const __grid_constant__ PixelParams P) {
-    using SM = typename TileShape<TS>::Smem;
+    using SM = typename TileShape<TS, Window<WIN>::HALO>::Smem;
     __shared__ SM sm;
     int tx, ty;
     tile_of_block(gridDim.x, gridDim.y, blockIdx.y * gridDim.x + blockIdx.x, tx, ty);

@@ -42,7 +42,7 @@ __device__ __forceinline__ void group_barrier(int group) {
 
 // pairs_sample for the view pairs q = SUB, SUB + T, ... < NP only (their
 // constants in kernel parameters), the same operations per pair.
-template <int NP, int T, int SUB, int NPL = (SUB < NP ? (NP - SUB + T - 1) / T : 0)>
+template <int NP, int T, int SUB, int PITCH, int NPL = (SUB < NP ? (NP - SUB + T - 1) / T : 0)>
 __device__ __forceinline__ void pairs_sample_sub(const PixelParams& P, float alpha, float beta, int cx,
                                                  float2 (&J)[NPL > 0 ? NPL : 1]) {
     float2 fx[NPL > 0 ? NPL : 1], fy[NPL > 0 ? NPL : 1], xn[NPL > 0 ? NPL : 1], yn[NPL > 0 ? NPL : 1];
@@ -51,9 +51,9 @@ __device__ __forceinline__ void pairs_sample_sub(const PixelParams& P, float alp
     for (int j = 0; j < NPL; ++j) {
         const int q = SUB + j * T;
         const PixelParams::ViewPair& VP = P.pairs[q];
-        const float2 Yx = fma2(av, col_table<NP>()[q][0][cx], fma2(bv, VP.R[1], VP.t[0]));
-        const float2 Yy = fma2(av, col_table<NP>()[q][1][cx], fma2(bv, VP.R[4], VP.t[1]));
-        const float2 Yz = fma2(av, col_table<NP>()[q][2][cx], fma2(bv, VP.R[7], VP.t[2]));
+        const float2 Yx = fma2(av, col_table<NP, PITCH>()[q][0][cx], fma2(bv, VP.R[1], VP.t[0]));
+        const float2 Yy = fma2(av, col_table<NP, PITCH>()[q][1][cx], fma2(bv, VP.R[4], VP.t[1]));
+        const float2 Yz = fma2(av, col_table<NP, PITCH>()[q][2][cx], fma2(bv, VP.R[7], VP.t[2]));
         const float2 q2 = fma2(Yx, Yx, mul2(Yz, Yz));
         const float2 rho = make_float2(sqrt_approx(q2.x), sqrt_approx(q2.y));
         const float2 dl = add2(rho, make_float2(fabsf(Yz.x), fabsf(Yz.y)));
@@ -127,7 +127,7 @@ __device__ __forceinline__ void pair_costs_sub(const PixelParams& P, const SM& s
         const float t = __fdividef(dn, den);
         const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
         const float alpha = t * cl, beta = -t * sm.row_sin[ly + o];
-        pairs_sample_sub<NP, T, SUB>(P, alpha, beta, lx + o, c0);
+        pairs_sample_sub<NP, T, SUB, SM::PITCH>(P, alpha, beta, lx + o, c0);
 #pragma unroll
         for (int j = 0; j < NPL; ++j) SJ[j] = SJJ[j] = SIJ[j] = pair(0.f);
         if (MY_ODD) c0o = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z);
@@ -153,7 +153,7 @@ __device__ __forceinline__ void pair_costs_sub(const PixelParams& P, const SM& s
             const float alpha = t * cl, beta = t * msl;
             const float2 w2 = pair(w), wI2 = pair(wI);
             float2 Jall[NPL > 0 ? NPL : 1];
-            pairs_sample_sub<NP, T, SUB>(P, alpha, beta, cx, Jall);
+            pairs_sample_sub<NP, T, SUB, SM::PITCH>(P, alpha, beta, cx, Jall);
 #pragma unroll
             for (int j = 0; j < NPL; ++j) {
                 const float2 Jc = add2(Jall[j], make_float2(-c0[j].x, -c0[j].y));
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
     pixel_split_kernel(const __grid_constant__ PixelParams P) {
     static_assert(T == 2 || T == 4, "two or four warps per pixel group");
     static_assert(NS >= 2, "view pairs");
-    using SM = TileSmemT<32, 8 / T, T>;
+    using SM = TileSmemT<32, 8 / T, T, Window<WIN>::HALO>;
     constexpr int PIX = 128 / T;  // pixels of one colour per block
     __shared__ SM sm;
     __shared__ float xc[2][NS * PIX];  // view costs of the current candidate, double-buffered
@@ -250,9 +250,9 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
             const int q = i / cols, c = i - q * cols;
             const PixelParams::ViewPair& VP = P.pairs[q];
             const float2 sn = pair(sm.col_sin[c]), cs = pair(sm.col_cos[c]);
-            col_table<NP>()[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
-            col_table<NP>()[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
-            col_table<NP>()[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
+            col_table<NP, SM::PITCH>()[q][0][c] = fma2(VP.R[0], sn, mul2(VP.R[2], cs));
+            col_table<NP, SM::PITCH>()[q][1][c] = fma2(VP.R[3], sn, mul2(VP.R[5], cs));
+            col_table<NP, SM::PITCH>()[q][2][c] = fma2(VP.R[6], sn, mul2(VP.R[8], cs));
         }
         __syncthreads();
     }
