@@ -155,6 +155,19 @@ __device__ __forceinline__ float sample_bilinear_half(cudaTextureObject_t tex, f
     return fmaf(fy, bot - top, top);
 }
 
+// ---- Sums of products with their rounding fixed by the source: each
+// multiply-add an explicit fmaf and each other product an explicit __fmul_rn,
+// which the compiler never fuses. Written as a * b + c * d, the compiler may
+// fuse either product depending on the code around it, and on low-variance
+// patches the two roundings move the NCC cost by up to 1e-4; with these the
+// cost of a plane at a pixel has the same bits in every kernel that
+// evaluates it.
+
+// a . b = a.z b.z + (a.y b.y + a.x b.x), fused from the x product outward.
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.z, b.z, fmaf(a.y, b.y, __fmul_rn(a.x, b.x))); }
+// a b - c d with a b fused.
+__device__ __forceinline__ float mul_sub(float a, float b, float c, float d) { return fmaf(a, b, -__fmul_rn(c, d)); }
+
 // ---- Two views at once: the same arithmetic on float2 pairs with the packed
 // FP32 instructions (fma/add/mul .f32x2), which issue once for both lanes.
 

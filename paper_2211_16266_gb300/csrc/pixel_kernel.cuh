@@ -50,6 +50,26 @@ constexpr int min_blocks_for(int ns) { return ns <= 4 ? 8 : ns <= 6 ? 7 : ns <= 
 // beat more resident warps once the per-view sums fill the registers.
 constexpr int pixel_min_blocks(int ns) { return ns <= 4 ? 5 : ns <= 8 ? 4 : ns <= 10 ? 3 : 4; }
 
+// Reference-side constants of one pixel (independent of the hypothesis).
+struct RefStats {
+    float Ip;    // centre intensity
+    float mu;    // weighted mean of the samples
+    float Sw;    // sum of weights
+    float SIc;   // sum w (I - mu)   (zero up to rounding)
+    float varI;  // Sw * sum w (I - mu)^2 - SIc^2
+};
+
+// Per-block scratch of the half-sweep's pooled candidate evaluation: each
+// pixel's reference statistics and the minimum (cost, candidate) key of its
+// neighbour candidates, and per warp the list of (lane, candidate) pairs that
+// need a cost evaluation.
+struct SweepPool {
+    unsigned long long key[BLOCK_THREADS];
+    RefStats st[BLOCK_THREADS];
+    unsigned char item[BLOCK_THREADS / 32][32 * 8];
+};
+struct NoPool {};
+
 // Shared memory of one tile of TW x TH reference pixels with a halo of HALO
 // pixels on each side (the window radius the tile serves: the largest, or
 // that of a fixed-window instance); every shape has (TW / 2) x TH pixels of
@@ -65,6 +85,8 @@ struct TileSmemT {
     float row_cos[ROWS], row_sin[ROWS];  // cos lat, sin lat
     float col_sin[PITCH], col_cos[PITCH];  // sin lon, cos lon
     float wsp[2 * HALO + 1];             // spatial log2-weight of offset index k
+    // candidate pooling of the one-thread-per-pixel half-sweep
+    typename std::conditional<TPP == 1, SweepPool, NoPool>::type pool;
 };
 using TileSmem = TileSmemT<TILE_W, TILE_H>;  // the batched and no-alloc kernels' shape
 
@@ -119,14 +141,6 @@ struct Window<2> {
     __device__ static constexpr int stride(const PixelParams&) { return 1; }
 };
 
-// Reference-side constants of one pixel (independent of the hypothesis).
-struct RefStats {
-    float Ip;    // centre intensity
-    float mu;    // weighted mean of the samples
-    float Sw;    // sum of weights
-    float SIc;   // sum w (I - mu)   (zero up to rounding)
-    float varI;  // Sw * sum w (I - mu)^2 - SIc^2
-};
 
 __device__ __forceinline__ float load_ref(const PixelParams& P, int x, int y) {
     const uint8_t* row = P.ref + (int64_t)y * P.ref_pitch;
@@ -209,7 +223,7 @@ __device__ __forceinline__ RefStats ref_stats(const PixelParams& P, const SM& sm
         }
     }
     st.SIc = SIc;
-    st.varI = Sw * SIIc - SIc * SIc;
+    st.varI = mul_sub(Sw, SIIc, SIc, SIc);
     return st;
 }
 
@@ -360,7 +374,7 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const SM& sm, 
                                             const RefStats& st, float3 rp, float d, float3 n) {
     const float eps = 1e-8f * st.Sw * st.Sw;
     if (st.varI < eps) return 2.0f;
-    const float dn = d * (n.x * rp.x + n.y * rp.y + n.z * rp.z);
+    const float dn = d * dot3(n, rp);
     const int K = P.K, R = P.radius, stp = P.stride;
     const int ac = K >> 1;  // centre-most sample first: its intensity centres each view
 
@@ -369,7 +383,7 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const SM& sm, 
         const int o = ac * stp - R;
         const float cl = sm.row_cos[ly + o];
         const float3 rq = make_float3(cl * sm.col_sin[lx + o], -sm.row_sin[ly + o], cl * sm.col_cos[lx + o]);
-        const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+        const float den = dot3(n, rq);
         if (!(den < -1e-6f)) return 2.0f;
         const float t = __fdividef(dn, den);
         const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
@@ -394,7 +408,7 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const SM& sm, 
             const float wI = w * (Iq - st.mu);
             const int cx = lx + b * stp - R;
             const float3 rq = make_float3(cl * sm.col_sin[cx], msl, cl * sm.col_cos[cx]);
-            const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+            const float den = dot3(n, rq);
             if (!(den < -1e-6f)) {
                 valid = false;
                 break;
@@ -405,8 +419,8 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const SM& sm, 
             for (int s = 0; s < NS; ++s) {
                 if (EXACT || s < P.S) {
                     const float Jc = view_sample<VA>(P.src[s], X, Y, Z) - c0[s];
-                    const float tw = w * Jc;
-                    SJ[s] += tw;
+                    const float tw = __fmul_rn(w, Jc);
+                    SJ[s] = __fadd_rn(SJ[s], tw);
                     SJJ[s] = fmaf(tw, Jc, SJJ[s]);
                     SIJ[s] = fmaf(wI, Jc, SIJ[s]);
                 }
@@ -420,8 +434,8 @@ __device__ __forceinline__ float plane_cost(const PixelParams& P, const SM& sm, 
     for (int s = 0; s < NS; ++s) {
         float c = 3.0f;  // unused slots sort last
         if (EXACT || s < P.S) {
-            const float varJ = st.Sw * SJJ[s] - SJ[s] * SJ[s];
-            const float cov = st.Sw * SIJ[s] - st.SIc * SJ[s];
+            const float varJ = mul_sub(st.Sw, SJJ[s], SJ[s], SJ[s]);
+            const float cov = mul_sub(st.Sw, SIJ[s], st.SIc, SJ[s]);
             if (varJ < eps) {
                 c = 2.0f;
             } else {
@@ -513,7 +527,7 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
     constexpr bool ODD = (NS & 1) != 0;
     const float eps = 1e-8f * st.Sw * st.Sw;
     if (st.varI < eps) return 2.0f;
-    const float dn = d * (n.x * rp.x + n.y * rp.y + n.z * rp.z);
+    const float dn = d * dot3(n, rp);
     const int K = Window<WIN>::K(P), R = Window<WIN>::R(P), stp = Window<WIN>::stride(P);
     const int ac = K >> 1;
 
@@ -523,7 +537,7 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
         const int o = ac * stp - R;
         const float cl = sm.row_cos[ly + o];
         const float3 rq = make_float3(cl * sm.col_sin[lx + o], -sm.row_sin[ly + o], cl * sm.col_cos[lx + o]);
-        const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+        const float den = dot3(n, rq);
         if (!(den < -1e-6f)) return 2.0f;
         const float t = __fdividef(dn, den);
         const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
@@ -547,7 +561,7 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
             const float wI = w * (Iq - st.mu);
             const int cx = lx + b * stp - R;
             const float3 rq = make_float3(cl * sm.col_sin[cx], msl, cl * sm.col_cos[cx]);
-            const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+            const float den = dot3(n, rq);
             // an invalid sample makes the cost 2; the loop runs on without a
             // branch (1 % faster than leaving it), its values are discarded
             valid = valid && (den < -1e-6f);
@@ -568,8 +582,8 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
             }
             if (ODD) {
                 const float Jc = view_sample<VA>(P.src[NS - 1], X, Y, Z) - c0o;
-                const float tw = w * Jc;
-                SJo += tw;
+                const float tw = __fmul_rn(w, Jc);
+                SJo = __fadd_rn(SJo, tw);
                 SJJo = fmaf(tw, Jc, SJJo);
                 SIJo = fmaf(wI, Jc, SIJo);
             }
@@ -579,8 +593,8 @@ __device__ __forceinline__ float plane_cost_paired(const PixelParams& P, const S
 
     float cs[NS];
     auto view_cost = [&](float sj, float sjj, float sij) {
-        const float varJ = st.Sw * sjj - sj * sj;
-        const float cov = st.Sw * sij - st.SIc * sj;
+        const float varJ = mul_sub(st.Sw, sjj, sj, sj);
+        const float cov = mul_sub(st.Sw, sij, st.SIc, sj);
         if (varJ < eps) return 2.0f;
         float ncc = cov * rsqrtf(st.varI * varJ);
         ncc = fminf(1.0f, fmaxf(-1.0f, ncc));
@@ -629,7 +643,7 @@ __device__ __forceinline__ float cost_of(const PixelParams& P, const SM& sm, int
 
 // Face the camera: n . r_p < 0 (|n . r_p| < 1e-3: replace by -r_p).
 __device__ __forceinline__ float3 face_camera(float3 n, float3 rp) {
-    const float c = n.x * rp.x + n.y * rp.y + n.z * rp.z;
+    const float c = dot3(n, rp);
     if (fabsf(c) < 1e-3f) return make_float3(-rp.x, -rp.y, -rp.z);
     if (c > 0.f) return make_float3(-n.x, -n.y, -n.z);
     return n;
@@ -643,10 +657,174 @@ __device__ __forceinline__ void random_plane(const PixelParams& P, size_t i, flo
     const float inv = fmaf(u.x, P.inv_dmin - P.inv_dmax, P.inv_dmax);
     d = 1.0f / inv;
     const float z = 1.0f - 2.0f * u.y;
-    const float rho = sqrtf(fmaxf(0.f, 1.0f - z * z));
+    const float rho = sqrtf(fmaxf(0.f, fmaf(-z, z, 1.0f)));
     float sp, cp;
     sincospif(2.0f * u.z, &sp, &cp);
     n = face_camera(make_float3(rho * cp, rho * sp, z), rp);
+}
+
+// Neighbour candidate k of pixel (x, y) (Sec. III-C): the plane of the k-th
+// opposite-colour neighbour re-intersected with this pixel's ray. False where
+// the neighbour lies outside the image, the plane does not face the ray or the
+// range leaves [d_min, d_max]. Every use computes it with this one function,
+// so equal inputs give equal bits.
+__device__ __forceinline__ bool neighbour_candidate(const PixelParams& P, int x, int y, float3 rp, int k,
+                                                    float& dc, float3& nc) {
+    const int qy = y + c_neighbors[P.table][k][1];
+    if (qy < 0 || qy >= P.H) return false;
+    const int qx = wrap_index(x + c_neighbors[P.table][k][0], P.W);
+    const size_t j = (size_t)qy * P.W + qx;
+    nc = make_float3(P.nx[j], P.ny[j], P.nz[j]);
+    const float den = dot3(nc, rp);
+    const float3 rq = pixel_bearing(qx, qy, P.W, P.H);
+    dc = P.depth[j] * dot3(nc, rq) / den;
+    return den < -1e-6f && dc >= P.d_min && dc <= P.d_max;
+}
+
+// Bit-for-bit equal planes (the cost is a deterministic function of them).
+__device__ __forceinline__ bool same_plane(float d0, float3 n0, float d1, float3 n1) {
+    return __float_as_uint(d0) == __float_as_uint(d1) && __float_as_uint(n0.x) == __float_as_uint(n1.x) &&
+           __float_as_uint(n0.y) == __float_as_uint(n1.y) && __float_as_uint(n0.z) == __float_as_uint(n1.z);
+}
+
+// Cost bits mapped so that unsigned order is float order (negative values
+// bit-inverted, the sign bit set on the others), and back.
+__device__ __forceinline__ unsigned ordered_bits(float c) {
+    const unsigned u = __float_as_uint(c);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered_bits(unsigned o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// One half-sweep over the pixels of `colour` in a tile (Sec. III-C): each
+// pixel tries its 8 neighbour candidates, then n_refine perturbations of the
+// best so far, and a candidate replaces the incumbent only if its cost is
+// strictly lower. Taken in that order, the neighbour phase ends on the
+// candidate of lowest cost, the first of equal ones, if that cost is below
+// the incumbent's; a candidate bit-identical to the incumbent or to an
+// earlier candidate can never be that one (its cost equals theirs), so it is
+// not evaluated. The other neighbour candidates of a warp's 32 pixels are
+// pooled and evaluated 32 at a time, each lane taking any pixel's candidate,
+// and every pixel keeps the minimum of (cost, candidate index) in shared
+// memory; then each pixel adopts that candidate if it wins and runs its
+// refinements. The maps equal those of trying all candidates in turn.
+template <int NS, bool EXACT, class VA, int WIN, class SM>
+__device__ __forceinline__ void sweep_pooled(const PixelParams& P, SM& sm, int bx, int by, int x, int y, int colour,
+                                             int iter) {
+    const bool active = x < P.W && y < P.H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx = x - bx + P.radius, ly = y - by + P.radius;
+    const size_t i = (size_t)y * P.W + x;
+    float bd = 0.f, bc = 0.f;
+    float3 bn = make_float3(0.f, 0.f, 0.f), rp = bn;
+    unsigned need = 0;
+    if (active) {
+        rp = make_float3(sm.row_cos[ly] * sm.col_sin[lx], -sm.row_sin[ly], sm.row_cos[ly] * sm.col_cos[lx]);
+        sm.pool.st[threadIdx.x] = ref_stats(P, sm, lx, ly);
+        bd = P.depth[i];
+        bn = make_float3(P.nx[i], P.ny[i], P.nz[i]);
+        bc = P.cost[i];
+        float cd[8];
+        float3 cn[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool ok = neighbour_candidate(P, x, y, rp, k, cd[k], cn[k]);
+            bool dup = same_plane(cd[k], cn[k], bd, bn);
+#pragma unroll
+            for (int m = 0; m < k; ++m) dup = dup || (((need >> m) & 1u) && same_plane(cd[k], cn[k], cd[m], cn[m]));
+            if (ok && !dup) need |= 1u << k;
+        }
+    }
+    sm.pool.key[threadIdx.x] = ~0ull;
+    // this lane's first slot in the warp's list: exclusive prefix of the counts
+    const int cnt = __popc(need);
+    int off = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, off, d);
+        if (lane >= d) off += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, off, 31);
+    off -= cnt;
+    unsigned char* items = sm.pool.item[warp];
+    for (unsigned m = need; m; m &= m - 1) items[off++] = (unsigned char)((lane << 3) | (__ffs(m) - 1));
+    __syncwarp();
+
+    const int pooled_rounds = (total + 31) >> 5;  // warp-uniform
+    const int n_jobs = pooled_rounds + P.n_refine;
+    const float span = P.inv_dmin - P.inv_dmax;
+    // the neighbour phase's winner, once every pooled evaluation has landed
+    auto adopt_best = [&]() {
+        __syncwarp();
+        const unsigned long long key = sm.pool.key[threadIdx.x];
+        if (active && key != ~0ull) {
+            const float c = from_ordered_bits((unsigned)(key >> 3));
+            if (c < bc) {
+                float dc;
+                float3 nc;
+                neighbour_candidate(P, x, y, rp, (int)(key & 7u), dc, nc);
+                bc = c;
+                bd = dc;
+                bn = nc;
+            }
+        }
+    };
+#pragma unroll 1
+    for (int r = 0; r < n_jobs; ++r) {
+        if (r == pooled_rounds) adopt_best();
+        // the job of this round: (pixel, plane)
+        bool job = false;
+        int jt = threadIdx.x, jx = x, jy = y, k = 0;
+        float3 jrp = rp;
+        float dc = 0.f;
+        float3 nc = make_float3(0.f, 0.f, 0.f);
+        if (r < pooled_rounds) {
+            const int idx = (r << 5) + lane;
+            if (idx < total) {
+                const int it = items[idx];
+                k = it & 7;
+                jt = (warp << 5) + (it >> 3);
+                const int otx = jt % (SM::W / 2), oty = jt / (SM::W / 2);
+                jy = by + oty;
+                jx = bx + 2 * otx + ((jy + colour) & 1);
+                job = true;
+            }
+        } else if (active) {
+            const int t = r - pooled_rounds;
+            const float sc = __int_as_float((126 - t) << 23);  // 2^-(t+1)
+            const U4 u = draw_uniform4(i, (uint64_t)iter, (uint64_t)(1 + t), P.seed, P.keyframe);
+            float inv = fmaf((2.0f * u.x - 1.0f) * sc, span, 1.0f / bd);
+            inv = fminf(P.inv_dmin, fmaxf(P.inv_dmax, inv));
+            dc = 1.0f / inv;
+            nc = make_float3(fmaf(sc, 2.0f * u.y - 1.0f, bn.x), fmaf(sc, 2.0f * u.z - 1.0f, bn.y),
+                             fmaf(sc, 2.0f * u.w - 1.0f, bn.z));
+            const float il = 1.0f / sqrtf(dot3(nc, nc));
+            nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
+            job = true;
+        }
+        if (!job) continue;
+        const int jlx = jx - bx + P.radius, jly = jy - by + P.radius;
+        if (r < pooled_rounds) {
+            jrp = make_float3(sm.row_cos[jly] * sm.col_sin[jlx], -sm.row_sin[jly], sm.row_cos[jly] * sm.col_cos[jlx]);
+            neighbour_candidate(P, jx, jy, jrp, k, dc, nc);
+        }
+        const float c = cost_of<NS, EXACT, VA, WIN, SM>(P, sm, jlx, jly, sm.pool.st[jt], jrp, dc, nc);
+        if (r < pooled_rounds) {
+            if (c == c) atomicMin(&sm.pool.key[jt], ((unsigned long long)ordered_bits(c) << 3) | (unsigned)k);
+        } else if (c < bc) {
+            bc = c;
+            bd = dc;
+            bn = nc;
+        }
+    }
+    if (n_jobs == pooled_rounds) adopt_best();
+    if (!active) return;
+    P.depth[i] = bd;
+    P.nx[i] = bn.x;
+    P.ny[i] = bn.y;
+    P.nz[i] = bn.z;
+    P.cost[i] = bc;
 }
 
 // One tile of one problem: stage the reference tile, then every active
@@ -675,6 +853,10 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, SM& sm, int b
     const int tx = threadIdx.x % (SM::W / 2), ty = threadIdx.x / (SM::W / 2);
     const int y = by + ty;
     const int x = bx + 2 * tx + ((y + colour) & 1);
+    if constexpr (MODE == MODE_SWEEP) {
+        sweep_pooled<NS, EXACT, VA, WIN, SM>(P, sm, bx, by, x, y, colour, iter);
+        return;
+    }
     if (x >= P.W || y >= P.H) return;
     const int lx = x - bx + P.radius, ly = y - by + P.radius;
     const size_t i = (size_t)y * P.W + x;
@@ -688,68 +870,14 @@ __device__ __forceinline__ void process_tile(const PixelParams& P, SM& sm, int b
         P.cost[i] = cost_of<NS, EXACT, VA, WIN, SM>(P, sm, lx, ly, st, rp, P.depth[i], n);
         return;
     }
-    if (MODE == MODE_INIT) {
-        float d;
-        float3 n;
-        random_plane(P, i, rp, d, n);
-        P.depth[i] = d;
-        P.nx[i] = n.x;
-        P.ny[i] = n.y;
-        P.nz[i] = n.z;
-        P.cost[i] = cost_of<NS, EXACT, VA, WIN, SM>(P, sm, lx, ly, st, rp, d, n);
-        return;
-    }
-
-    // MODE_SWEEP: 8 neighbour planes, then n_refine perturbations of the
-    // current best (Sec. III-C); strictly lower cost wins.
-    float bd = P.depth[i];
-    float3 bn = make_float3(P.nx[i], P.ny[i], P.nz[i]);
-    float bc = P.cost[i];
-    const float span = P.inv_dmin - P.inv_dmax;
-    const int n_cand = 8 + P.n_refine;
-#pragma unroll 1
-    for (int k = 0; k < n_cand; ++k) {
-        float dc;
-        float3 nc;
-        bool ok = true;
-        if (k < 8) {
-            const int qy = y + c_neighbors[P.table][k][1];
-            ok = qy >= 0 && qy < P.H;
-            if (ok) {
-                const int qx = wrap_index(x + c_neighbors[P.table][k][0], P.W);
-                const size_t j = (size_t)qy * P.W + qx;
-                nc = make_float3(P.nx[j], P.ny[j], P.nz[j]);
-                const float den = nc.x * rp.x + nc.y * rp.y + nc.z * rp.z;
-                const float3 rq = pixel_bearing(qx, qy, P.W, P.H);
-                dc = P.depth[j] * (nc.x * rq.x + nc.y * rq.y + nc.z * rq.z) / den;
-                ok = den < -1e-6f && dc >= P.d_min && dc <= P.d_max;
-            }
-        } else {
-            const int t = k - 8;
-            const float s = __int_as_float((126 - t) << 23);  // 2^-(t+1)
-            const U4 u = draw_uniform4(i, (uint64_t)iter, (uint64_t)(1 + t), P.seed, P.keyframe);
-            float inv = fmaf((2.0f * u.x - 1.0f) * s, span, 1.0f / bd);
-            inv = fminf(P.inv_dmin, fmaxf(P.inv_dmax, inv));
-            dc = 1.0f / inv;
-            nc = make_float3(fmaf(s, 2.0f * u.y - 1.0f, bn.x), fmaf(s, 2.0f * u.z - 1.0f, bn.y),
-                             fmaf(s, 2.0f * u.w - 1.0f, bn.z));
-            const float il = 1.0f / sqrtf(nc.x * nc.x + nc.y * nc.y + nc.z * nc.z);
-            nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
-        }
-        if (ok) {
-            const float c = cost_of<NS, EXACT, VA, WIN, SM>(P, sm, lx, ly, st, rp, dc, nc);
-            if (c < bc) {
-                bc = c;
-                bd = dc;
-                bn = nc;
-            }
-        }
-    }
-    P.depth[i] = bd;
-    P.nx[i] = bn.x;
-    P.ny[i] = bn.y;
-    P.nz[i] = bn.z;
-    P.cost[i] = bc;
+    float d;
+    float3 n;
+    random_plane(P, i, rp, d, n);
+    P.depth[i] = d;
+    P.nx[i] = n.x;
+    P.ny[i] = n.y;
+    P.nz[i] = n.z;
+    P.cost[i] = cost_of<NS, EXACT, VA, WIN, SM>(P, sm, lx, ly, st, rp, d, n);
 }
 
 template <int NS, bool EXACT, int MODE, int WIN = 0, int TS = 0>

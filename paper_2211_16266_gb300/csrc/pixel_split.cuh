@@ -109,7 +109,7 @@ __device__ __forceinline__ void pair_costs_sub(const PixelParams& P, const SM& s
         store_all(2.0f);
         return;
     }
-    const float dn = d * (n.x * rp.x + n.y * rp.y + n.z * rp.z);
+    const float dn = d * dot3(n, rp);
     const int K = Window<WIN>::K(P), R = Window<WIN>::R(P), stp = Window<WIN>::stride(P);
     const int ac = K >> 1;
 
@@ -119,7 +119,7 @@ __device__ __forceinline__ void pair_costs_sub(const PixelParams& P, const SM& s
         const int o = ac * stp - R;
         const float cl = sm.row_cos[ly + o];
         const float3 rq = make_float3(cl * sm.col_sin[lx + o], -sm.row_sin[ly + o], cl * sm.col_cos[lx + o]);
-        const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+        const float den = dot3(n, rq);
         if (!(den < -1e-6f)) {
             store_all(2.0f);
             return;
@@ -146,7 +146,7 @@ __device__ __forceinline__ void pair_costs_sub(const PixelParams& P, const SM& s
             const float wI = w * (Iq - st.mu);
             const int cx = lx + b * stp - R;
             const float3 rq = make_float3(cl * sm.col_sin[cx], msl, cl * sm.col_cos[cx]);
-            const float den = n.x * rq.x + n.y * rq.y + n.z * rq.z;
+            const float den = dot3(n, rq);
             valid = valid && (den < -1e-6f);
             const float t = __fdividef(dn, den);
             const float X = t * rq.x, Y = t * rq.y, Z = t * rq.z;
@@ -164,8 +164,8 @@ __device__ __forceinline__ void pair_costs_sub(const PixelParams& P, const SM& s
             }
             if (MY_ODD) {
                 const float Jc = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z) - c0o;
-                const float tw = w * Jc;
-                SJo += tw;
+                const float tw = __fmul_rn(w, Jc);
+                SJo = __fadd_rn(SJo, tw);
                 SJJo = fmaf(tw, Jc, SJJo);
                 SIJo = fmaf(wI, Jc, SIJo);
             }
@@ -176,8 +176,8 @@ __device__ __forceinline__ void pair_costs_sub(const PixelParams& P, const SM& s
         return;
     }
     auto view_cost = [&](float sj, float sjj, float sij) {
-        const float varJ = st.Sw * sjj - sj * sj;
-        const float cov = st.Sw * sij - st.SIc * sj;
+        const float varJ = mul_sub(st.Sw, sjj, sj, sj);
+        const float cov = mul_sub(st.Sw, sij, st.SIc, sj);
         if (varJ < eps) return 2.0f;
         float ncc = cov * rsqrtf(st.varI * varJ);
         ncc = fminf(1.0f, fmaxf(-1.0f, ncc));
@@ -292,9 +292,9 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
                 const int qx = wrap_index(x + c_neighbors[P.table][k][0], P.W);
                 const size_t j = (size_t)qy * P.W + qx;
                 nc = make_float3(P.nx[j], P.ny[j], P.nz[j]);
-                const float den = nc.x * rp.x + nc.y * rp.y + nc.z * rp.z;
+                const float den = dot3(nc, rp);
                 const float3 rq = pixel_bearing(qx, qy, P.W, P.H);
-                dc = P.depth[j] * (nc.x * rq.x + nc.y * rq.y + nc.z * rq.z) / den;
+                dc = P.depth[j] * dot3(nc, rq) / den;
                 ok = den < -1e-6f && dc >= P.d_min && dc <= P.d_max;
             }
         } else if (ok) {
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, split_min_blocks(NS, T))
             dc = 1.0f / inv;
             nc = make_float3(fmaf(s, 2.0f * u.y - 1.0f, bn.x), fmaf(s, 2.0f * u.z - 1.0f, bn.y),
                              fmaf(s, 2.0f * u.w - 1.0f, bn.z));
-            const float il = 1.0f / sqrtf(nc.x * nc.x + nc.y * nc.y + nc.z * nc.z);
+            const float il = 1.0f / sqrtf(dot3(nc, nc));
             nc = face_camera(make_float3(nc.x * il, nc.y * il, nc.z * il), rp);
         }
         if (ok) view_costs_split<NS, T, WIN>(sub, P, sm, lx, ly, st, rp, dc, nc, xc[par], pix, PIX);
