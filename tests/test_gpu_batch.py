@@ -189,7 +189,10 @@ def test_threads_per_pixel_match_the_oracle(pm, ctx, tpp):
     whole densification within the bar (cost 1e-4, range 0.5 % on 99.5 % of
     pixels). Problems: 6 views (3 pairs: uneven over 2 warps, one warp idle at
     4), 7 views in fp16 (an odd view), 12 views (6 pairs: 3 per warp at 2,
-    uneven at 4), ragged tiles."""
+    uneven at 4), ragged tiles. The split kernels try every neighbour candidate
+    in turn, while the one-thread kernel skips the bit-identical ones and pools
+    the rest across the warp, so the equality also checks that pooling and
+    skipping leave the maps unchanged."""
     p1 = scenes.config1(W=384, H=192)
     p2 = scenes.trajectory_problem(250, 130, 7, seed_scene=1016, fmt="f16")
     p2.params = dict(p1.params, iterations=3, best_k=2, keyframe_id=41)
