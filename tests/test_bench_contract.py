@@ -41,7 +41,12 @@ def test_reference_arm_prints_one_contract_line(monkeypatch):
     assert (d["metric"], d["unit"], d["n_gpus"], d["steps"], d["warmup"]) == (bench.METRIC, "keyframes/s", 1, 2, 1)
     assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
     assert d["data"] == "synthetic" and isinstance(d["dtype"], str)
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    assert d["value"] > 0
+    # a step is the bounded sample: its wall time is ms_per_step, and the value comes
+    # from the keyframe time the sample scales to
+    cb = d["cpu_baseline"]
+    assert abs(d["ms_per_step"] - 1e3 * cb["sample_s_per_step"]) < 1e-6 * d["ms_per_step"]
+    assert abs(cb["keyframe_s_scaled"] - 1.0 / d["value"]) < 1e-6 * cb["keyframe_s_scaled"]
     assert d["config"] == bench.keyframe_config(1) and "workload" in d["config"] and "model" not in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["unit"] == d["unit"]
