@@ -344,7 +344,7 @@ def precision_forms(reps=3, n_sample=300):
 
 
 # The autotuner's pick on the 32-keyframe fp16 batch (bench.py --workload batched):
-# pmsp_tuning(blocks_per_sm, order, patch_stride, strategy, tile, tpp).
+# pmsp_tuning(blocks_per_sm, order, patch_stride, strategy, tile, tpp, lanes).
 BATCH_TUNING = (0, 0, 0, 1, 0, 1)
 
 
@@ -633,7 +633,7 @@ def batched_forms(formats=("f16", "u8", "f32"), reps=3, tuning=None):
                 stream.synchronize()
                 acc["batched_f16"] = accuracy(outs, gts)
                 used = dict(blocks_per_sm=t.blocks_per_sm, order=t.order, patch_stride=t.patch_stride,
-                            strategy=t.strategy, tile=t.tile, tpp=t.tpp)
+                            strategy=t.strategy, tile=t.tile, tpp=t.tpp, lanes=t.lanes)
             res[f"plain_{fmt}"] = timed(plain, reps)
             stream.synchronize()
             acc[f"plain_{fmt}"] = accuracy(outs, gts)

@@ -393,10 +393,15 @@ typedef struct {
                               reference pixels per 128-thread block, 0: 32x8, 1: 64x4, 2: 16x16
                               (every shape computes the same numbers) */
     int32_t tpp;           /* strategy 1, half-sweeps of keyframes with 2 or more sources:
-                              threads per pixel, 0 or 1: one; 2 or 4: the pixel's view pairs
-                              split over 2 or 4 warps that exchange their view costs through
-                              shared memory; the same numbers, fewer registers per thread
+                              threads per pixel, 0 or 1: one; 2 or 4: split as `lanes` says
                               (tile 32x4 or 32x2, `tile` ignored); 0, 1, 2 or 4, else
+                              PMSP_EINVAL */
+    int32_t lanes;         /* how tpp 2 or 4 splits a pixel: 0: its view pairs over 2 or 4
+                              warps that exchange their view costs through shared memory (the
+                              same numbers as one thread, fewer registers per thread); 1: its
+                              patch samples over 2 or 4 adjacent lanes of one warp whose NCC
+                              sums are added by warp shuffles (the sums in another order:
+                              equal within rounding, not bit for bit); 0 or 1, else
                               PMSP_EINVAL */
 } pmsp_tuning;
 

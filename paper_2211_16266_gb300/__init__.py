@@ -112,7 +112,8 @@ class pmsp_batch_item(ctypes.Structure):
 
 class pmsp_tuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("order", ctypes.c_int32), ("patch_stride", ctypes.c_int32),
-                ("strategy", ctypes.c_int32), ("tile", ctypes.c_int32), ("tpp", ctypes.c_int32)]
+                ("strategy", ctypes.c_int32), ("tile", ctypes.c_int32), ("tpp", ctypes.c_int32),
+                ("lanes", ctypes.c_int32)]
 
 
 class pmsp_peaks(ctypes.Structure):

@@ -181,7 +181,7 @@ static int build_plan(pmsp_ctx* c, BatchEngine& b, const pmsp_batch_item* items,
         fill_problem(P, &it.ref, ref_dev, pitch, &it.ref_pose, it.srcs, tex, it.src_poses, it.n_src, &p);
         P.err = c->d_err;
         P.tile = t.strategy == 1 ? t.tile : 0;
-        P.tpp = t.strategy == 1 && t.tpp > 1 ? t.tpp : 1;
+        P.tpp = t.strategy == 1 && t.tpp > 1 ? (t.lanes ? -t.tpp : t.tpp) : 1;
         const size_t N = (size_t)it.ref.w * it.ref.h;
         if (it.out.memory == PMSP_DEVICE) {
             P.depth = it.out.depth;
@@ -380,11 +380,12 @@ int pmsp_densify_batch(pmsp_ctx* c, const pmsp_batch_item* items, int n, uint32_
         all_device = all_device && items[i].ref.memory == PMSP_DEVICE && items[i].out.memory == PMSP_DEVICE;
         for (int s = 0; s < items[i].n_src; ++s) all_device = all_device && items[i].srcs[s].memory == PMSP_DEVICE;
     }
-    pmsp_tuning t{0, 0, 0, 0, 0, 0};
+    pmsp_tuning t{0, 0, 0, 0, 0, 0, 0};
     if (tuning) t = *tuning;
     if (t.tile < 0 || t.tile > 2) return ctx_fail(c, PMSP_EINVAL, "tuning: tile %d outside [0, 2]", t.tile);
     if (t.tpp != 0 && t.tpp != 1 && t.tpp != 2 && t.tpp != 4)
         return ctx_fail(c, PMSP_EINVAL, "tuning: tpp %d not 1, 2 or 4", t.tpp);
+    if (t.lanes != 0 && t.lanes != 1) return ctx_fail(c, PMSP_EINVAL, "tuning: lanes %d not 0 or 1", t.lanes);
     BatchEngine& b = engine(c);
     if (b.tex.size() > 1024) {  // bound the texture cache: start over
         cudaStreamSynchronize(c->stream);
@@ -474,12 +475,12 @@ int pmsp_autotune(pmsp_ctx* c, const pmsp_batch_item* items, int n, float max_ch
         ms = f;
         return r;
     };
-    pmsp_tuning best{0, 0, 0, 0, 0, 0};
+    pmsp_tuning best{0, 0, 0, 0, 0, 0, 0};
     double best_ms = 1e30;
     std::vector<int> bps_list;
     for (int k = occ; k >= 1 && (int)bps_list.size() < 4; --k) bps_list.push_back(k);
     for (int tile = 0; tile < 3; ++tile) {
-        pmsp_tuning t{0, 0, 0, 1, tile, 1};  // concurrent per-keyframe chains, each tile shape
+        pmsp_tuning t{0, 0, 0, 1, tile, 1, 0};  // concurrent per-keyframe chains, each tile shape
         double ms;
         if ((rc = time_run(t, ms)) || (rc = time_run(t, ms))) return rc;
         if (ms < best_ms) {
@@ -487,18 +488,21 @@ int pmsp_autotune(pmsp_ctx* c, const pmsp_batch_item* items, int n, float max_ch
             best = t;
         }
     }
-    for (int tpp : {2, 4}) {  // per-keyframe chains with the views split over 2 or 4 warps per pixel
-        pmsp_tuning t{0, 0, 0, 1, 0, tpp};
-        double ms;
-        if ((rc = time_run(t, ms)) || (rc = time_run(t, ms))) return rc;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = t;
+    // per-keyframe chains with 2 or 4 threads per pixel: the views split over
+    // warps, or the patch samples over adjacent lanes
+    for (int lanes = 0; lanes < 2; ++lanes)
+        for (int tpp : {2, 4}) {
+            pmsp_tuning t{0, 0, 0, 1, 0, tpp, lanes};
+            double ms;
+            if ((rc = time_run(t, ms)) || (rc = time_run(t, ms))) return rc;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
         }
-    }
     for (int order = 0; order < 2; ++order)
         for (int bps : bps_list) {
-            pmsp_tuning t{bps, order, 0, 0, 0, 0};
+            pmsp_tuning t{bps, order, 0, 0, 0, 0, 0};
             double ms;
             if ((rc = time_run(t, ms))) return rc;  // first run of each setting also warms caches
             if ((rc = time_run(t, ms))) return rc;

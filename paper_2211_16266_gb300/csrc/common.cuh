@@ -65,7 +65,8 @@ struct alignas(16) PixelParams {
     unsigned long long seed, keyframe;
     int phase;            // batched serving: 0,1 initialisation colours, 2 + 2 t + c half-sweep (t, c)
     int tile;             // tile shape of the single-keyframe half-sweep: 0 32x8, 1 64x4, 2 16x16
-    int tpp;              // threads (warps) per pixel of the single-keyframe half-sweep: 1, 2 or 4
+    int tpp;              // threads per pixel of the single-keyframe half-sweep: 1; 2 or 4 warps
+                          // (views split); -2 or -4: adjacent lanes (patch samples split)
     int colour;
     int iter;
     unsigned* err;

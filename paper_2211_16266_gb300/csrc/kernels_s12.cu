@@ -1,4 +1,5 @@
 // Instantiation of the per-pixel kernels for exactly 12 source views.
+#include "pixel_lanes.cuh"
 #include "pixel_split.cuh"
 
 namespace pmsp {

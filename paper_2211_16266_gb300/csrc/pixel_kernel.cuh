@@ -913,9 +913,13 @@ __host__ __device__ inline int window_of(const PixelParams& p) {
     return 0;
 }
 
-// Half-sweeps with 2 or 4 threads (warps) per pixel, pixel_split.cuh.
+// Half-sweeps with 2 or 4 threads per pixel: the views split over warps
+// (pixel_split.cuh, PixelParams::tpp 2 or 4) or the patch samples split over
+// adjacent lanes (pixel_lanes.cuh, tpp -2 or -4).
 template <int NS, bool EXACT>
 cudaError_t launch_split_sweep(const PixelParams& p, cudaStream_t stream);
+template <int NS, bool EXACT>
+cudaError_t launch_lanes_sweep(const PixelParams& p, cudaStream_t stream);
 
 template <int NS, bool EXACT>
 cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t stream) {
@@ -925,8 +929,10 @@ cudaError_t launch_pixel_kernel_ns(const PixelParams& p, int mode, cudaStream_t 
         case MODE_INIT: pixel_kernel<NS, EXACT, MODE_INIT><<<grid, BLOCK_THREADS, 0, stream>>>(p); break;
         default:
             // views split over several warps per pixel (a tuning choice; same maps)
-            if constexpr (EXACT && NS >= 2)
+            if constexpr (EXACT && NS >= 2) {
                 if (p.tpp > 1) return launch_split_sweep<NS, EXACT>(p, stream);
+                if (p.tpp < -1) return launch_lanes_sweep<NS, EXACT>(p, stream);
+            }
             // the half-sweep dominates the run time: fixed-window instances for the
             // paired path (exact view counts of at least 2), in three tile shapes
             if constexpr (EXACT && NS >= 2) {

@@ -215,14 +215,69 @@ def test_threads_per_pixel_match_the_oracle(pm, ctx, tpp):
         assert np.mean(np.abs(gc - oc) <= 1e-4) >= 0.995
 
 
+_LANE_ORACLE = {}
+
+
+def _lane_problems():
+    """Whole densifications for the lane split, with the FP64 oracle's maps (computed
+    once for both lane counts)."""
+    p1 = scenes.config1(W=384, H=192)
+    p2 = scenes.trajectory_problem(250, 130, 7, seed_scene=1016, fmt="f16")
+    p2.params = dict(p1.params, iterations=3, best_k=2, keyframe_id=41)
+    p3 = scenes.trajectory_problem(96, 48, 12, seed_scene=1014)
+    p3.params = dict(d_min=0.3, d_max=10.0, patch_w=11, patch_stride=2, iterations=2, best_k=4, sigma_color=0.2,
+                     sigma_space=3.0, n_refine=6, neighbor_table=0, seed=3, keyframe_id=21)
+    p4 = scenes.trajectory_problem(200, 100, 4, seed_scene=1017)
+    p4.params = dict(p1.params, patch_w=5, patch_stride=1, iterations=3, best_k=2, keyframe_id=43)
+    p5 = scenes.trajectory_problem(160, 80, 3, seed_scene=1018)
+    p5.params = dict(p1.params, patch_w=3, patch_stride=1, iterations=3, best_k=1, sigma_color=0.0,
+                     sigma_space=0.0, keyframe_id=44)
+    probs = [p1, p2, p3, p4, p5]
+    for k, p in enumerate(probs):
+        if k not in _LANE_ORACLE:
+            _LANE_ORACLE[k] = oracle.Problem.from_scene(p).densify()
+    return probs, [_LANE_ORACLE[k] for k in range(len(probs))]
+
+
+@pytest.mark.parametrize("tpp", [2, 4])
+def test_lane_split_matches_the_oracle(pm, ctx, tpp):
+    """Half-sweeps with each pixel's patch samples split over tpp adjacent lanes of
+    a warp (lane `sub` takes the samples sub, sub + tpp, ... of the window in
+    row-major order, every lane the centre sample), whose four NCC sums per view
+    and validity flag are combined by __shfl_xor_sync butterflies: the FP64
+    oracle's whole densification within the bar (cost 1e-4, range 0.5 % on 99.5 %
+    of pixels), and the one-thread maps within the same bar (the sums are added in
+    another order, so not bit for bit). Problems: 6 views at 11x11 / 2 (35 samples
+    besides the centre: 18 / 17 over 2 lanes, 9 / 8 over 4), 7 views in fp16 (an
+    odd view), 12 views (6 pairs), 4 views with a dense 5x5 window and 3 views with
+    a 3x3 window and no bilateral weights (the generic window loop; at 3x3 a lane's
+    samples wrap across rows), all with ragged tiles."""
+    probs, ref = _lane_problems()
+    args = [_args(p) for p in probs]
+    one = pm.pmsp_densify_batch(ctx, pm.Batch([(*a, p.params, None) for a, p in zip(args, probs)]),
+                                tuning=pm.pmsp_tuning(0, 0, 0, 1, 0, 1))
+    one = [o.numpy() for o in one]
+    outs = pm.pmsp_densify_batch(ctx, pm.Batch([(*a, p.params, None) for a, p in zip(args, probs)]),
+                                 tuning=pm.pmsp_tuning(0, 0, 0, 1, 0, tpp, 1))
+    for p, (wd, wn, wc), o, (od, on, oc) in zip(probs, one, outs, ref):
+        gd, gn, gc = (a.astype(np.float64) for a in o.numpy())
+        assert np.mean(np.abs(gd - od) / od <= 5e-3) >= 0.995
+        assert np.mean(np.abs(gc - oc) <= 1e-4) >= 0.995
+        assert np.mean(np.abs(gd - wd) / wd <= 5e-3) >= 0.995
+        assert np.mean(np.abs(gc - wc) <= 1e-4) >= 0.995
+
+
 def test_invalid_tuning_is_refused(pm, ctx):
-    """Threads per pixel other than 0, 1, 2 or 4 and tile shapes outside 0..2 are
-    refused with PMSP_EINVAL before anything runs; the context stays usable."""
+    """Threads per pixel other than 0, 1, 2 or 4, a lane flag other than 0 or 1 and
+    tile shapes outside 0..2 are refused with PMSP_EINVAL before anything runs; the
+    context stays usable."""
     p = scenes.config0(W=64, H=32)
     args = _args(p)
-    for bad in (pm.pmsp_tuning(0, 0, 0, 1, 0, 3), pm.pmsp_tuning(0, 0, 0, 1, 0, 8), pm.pmsp_tuning(0, 0, 0, 1, 3, 1)):
+    for bad in (pm.pmsp_tuning(0, 0, 0, 1, 0, 3), pm.pmsp_tuning(0, 0, 0, 1, 0, 8), pm.pmsp_tuning(0, 0, 0, 1, 3, 1),
+                pm.pmsp_tuning(0, 0, 0, 1, 0, 2, 2), pm.pmsp_tuning(0, 0, 0, 1, 0, 2, -1)):
         with pytest.raises(pm.PmspError) as e:
             pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=bad)
         assert e.value.code == pm.PMSP_EINVAL
     pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=pm.pmsp_tuning(0, 0, 0, 1, 0, 2))
+    pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=pm.pmsp_tuning(0, 0, 0, 1, 0, 4, 1))
     pm.pmsp_sync(ctx)
