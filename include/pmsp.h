@@ -393,14 +393,14 @@ typedef struct {
                               reference pixels per 128-thread block, 0: 32x8, 1: 64x4, 2: 16x16
                               (every shape computes the same numbers) */
     int32_t tpp;           /* strategy 1, half-sweeps of keyframes with 2 or more sources:
-                              threads per pixel, 0 or 1: one; 2 or 4: split as `lanes` says
-                              (tile 32x4 or 32x2, `tile` ignored); 0, 1, 2 or 4, else
-                              PMSP_EINVAL */
-    int32_t lanes;         /* how tpp 2 or 4 splits a pixel: 0: its view pairs over 2 or 4
+                              threads per pixel, 0 or 1: one; 2, 4 (or 8 with `lanes` 1):
+                              split as `lanes` says (tile 32x4, 32x2 or 32x1, `tile`
+                              ignored); 0, 1, 2, 4, or 8 with lanes, else PMSP_EINVAL */
+    int32_t lanes;         /* how tpp 2 or more splits a pixel: 0: its view pairs over 2 or 4
                               warps that exchange their view costs through shared memory (the
                               same numbers as one thread, fewer registers per thread); 1: its
-                              patch samples over 2 or 4 adjacent lanes of one warp whose NCC
-                              sums are added by warp shuffles (the sums in another order:
+                              patch samples over 2, 4 or 8 adjacent lanes of one warp whose
+                              NCC sums are added by warp shuffles (the sums in another order:
                               equal within rounding, not bit for bit); 0 or 1, else
                               PMSP_EINVAL */
 } pmsp_tuning;

@@ -383,9 +383,9 @@ int pmsp_densify_batch(pmsp_ctx* c, const pmsp_batch_item* items, int n, uint32_
     pmsp_tuning t{0, 0, 0, 0, 0, 0, 0};
     if (tuning) t = *tuning;
     if (t.tile < 0 || t.tile > 2) return ctx_fail(c, PMSP_EINVAL, "tuning: tile %d outside [0, 2]", t.tile);
-    if (t.tpp != 0 && t.tpp != 1 && t.tpp != 2 && t.tpp != 4)
-        return ctx_fail(c, PMSP_EINVAL, "tuning: tpp %d not 1, 2 or 4", t.tpp);
     if (t.lanes != 0 && t.lanes != 1) return ctx_fail(c, PMSP_EINVAL, "tuning: lanes %d not 0 or 1", t.lanes);
+    if (t.tpp != 0 && t.tpp != 1 && t.tpp != 2 && t.tpp != 4 && !(t.tpp == 8 && t.lanes == 1))
+        return ctx_fail(c, PMSP_EINVAL, "tuning: tpp %d not 1, 2 or 4 (or 8 with lanes)", t.tpp);
     BatchEngine& b = engine(c);
     if (b.tex.size() > 1024) {  // bound the texture cache: start over
         cudaStreamSynchronize(c->stream);
@@ -491,7 +491,8 @@ int pmsp_autotune(pmsp_ctx* c, const pmsp_batch_item* items, int n, float max_ch
     // per-keyframe chains with 2 or 4 threads per pixel: the views split over
     // warps, or the patch samples over adjacent lanes
     for (int lanes = 0; lanes < 2; ++lanes)
-        for (int tpp : {2, 4}) {
+        for (int tpp : {2, 4, 8}) {
+            if (tpp == 8 && !lanes) continue;  // the warp split serves 2 or 4 warps
             pmsp_tuning t{0, 0, 0, 1, 0, tpp, lanes};
             double ms;
             if ((rc = time_run(t, ms)) || (rc = time_run(t, ms))) return rc;

@@ -66,7 +66,7 @@ struct alignas(16) PixelParams {
     int phase;            // batched serving: 0,1 initialisation colours, 2 + 2 t + c half-sweep (t, c)
     int tile;             // tile shape of the single-keyframe half-sweep: 0 32x8, 1 64x4, 2 16x16
     int tpp;              // threads per pixel of the single-keyframe half-sweep: 1; 2 or 4 warps
-                          // (views split); -2 or -4: adjacent lanes (patch samples split)
+                          // (views split); -2, -4 or -8: adjacent lanes (patch samples split)
     int colour;
     int iter;
     unsigned* err;

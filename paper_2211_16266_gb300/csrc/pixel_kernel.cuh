@@ -915,7 +915,7 @@ __host__ __device__ inline int window_of(const PixelParams& p) {
 
 // Half-sweeps with 2 or 4 threads per pixel: the views split over warps
 // (pixel_split.cuh, PixelParams::tpp 2 or 4) or the patch samples split over
-// adjacent lanes (pixel_lanes.cuh, tpp -2 or -4).
+// adjacent lanes (pixel_lanes.cuh, tpp -2, -4 or -8).
 template <int NS, bool EXACT>
 cudaError_t launch_split_sweep(const PixelParams& p, cudaStream_t stream);
 template <int NS, bool EXACT>

@@ -1,5 +1,5 @@
 // Half-sweep with the patch samples of one pixel split over T adjacent lanes
-// of a warp (T = 2 or 4), the NCC sums combined by warp shuffles.
+// of a warp (T = 2, 4 or 8), the NCC sums combined by warp shuffles.
 //
 // Lane `sub` of a pixel group takes the samples m = sub, sub + T, ... of the
 // window (row-major order, the centre sample excluded) and accumulates every
@@ -182,7 +182,7 @@ __device__ __forceinline__ float plane_cost_lanes(const PixelParams& P, const SM
 template <int NS, int T, int WIN>
 __global__ void __launch_bounds__(BLOCK_THREADS, pixel_min_blocks(NS))
     pixel_lanes_kernel(const __grid_constant__ PixelParams P) {
-    static_assert(T == 2 || T == 4, "two or four lanes per pixel");
+    static_assert(T == 2 || T == 4 || T == 8, "two, four or eight lanes per pixel");
     static_assert(NS >= 2, "view pairs");
     using SM = TileSmemT<32, 8 / T, T, Window<WIN>::HALO>;
     __shared__ SM sm;
@@ -263,10 +263,11 @@ inline cudaError_t launch_lanes_sweep_t(const PixelParams& p, cudaStream_t strea
     return cudaGetLastError();
 }
 
-// PixelParams::tpp = -2 or -4 selects this half-sweep.
+// PixelParams::tpp = -2, -4 or -8 selects this half-sweep.
 template <int NS, bool EXACT>
 cudaError_t launch_lanes_sweep(const PixelParams& p, cudaStream_t stream) {
     static_assert(EXACT, "the lane-split half-sweep serves exact view counts");
+    if (p.tpp <= -8) return launch_lanes_sweep_t<NS, 8>(p, stream);
     return p.tpp <= -4 ? launch_lanes_sweep_t<NS, 4>(p, stream) : launch_lanes_sweep_t<NS, 2>(p, stream);
 }
 

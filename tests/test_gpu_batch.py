@@ -239,16 +239,17 @@ def _lane_problems():
     return probs, [_LANE_ORACLE[k] for k in range(len(probs))]
 
 
-@pytest.mark.parametrize("tpp", [2, 4])
+@pytest.mark.parametrize("tpp", [2, 4, 8])
 def test_lane_split_matches_the_oracle(pm, ctx, tpp):
     """Half-sweeps with each pixel's patch samples split over tpp adjacent lanes of
     a warp (lane `sub` takes the samples sub, sub + tpp, ... of the window in
-    row-major order, every lane the centre sample), whose four NCC sums per view
+    row-major order, every lane the centre sample; 32x4, 32x2 or 32x1 tiles), whose four
+    NCC sums per view
     and validity flag are combined by __shfl_xor_sync butterflies: the FP64
     oracle's whole densification within the bar (cost 1e-4, range 0.5 % on 99.5 %
     of pixels), and the one-thread maps within the same bar (the sums are added in
     another order, so not bit for bit). Problems: 6 views at 11x11 / 2 (35 samples
-    besides the centre: 18 / 17 over 2 lanes, 9 / 8 over 4), 7 views in fp16 (an
+    besides the centre: 18 / 17 over 2 lanes, 9 / 8 over 4, 5 / 4 over 8), 7 views in fp16 (an
     odd view), 12 views (6 pairs), 4 views with a dense 5x5 window and 3 views with
     a 3x3 window and no bilateral weights (the generic window loop; at 3x3 a lane's
     samples wrap across rows), all with ragged tiles."""
@@ -268,16 +269,18 @@ def test_lane_split_matches_the_oracle(pm, ctx, tpp):
 
 
 def test_invalid_tuning_is_refused(pm, ctx):
-    """Threads per pixel other than 0, 1, 2 or 4, a lane flag other than 0 or 1 and
-    tile shapes outside 0..2 are refused with PMSP_EINVAL before anything runs; the
-    context stays usable."""
+    """Threads per pixel other than 0, 1, 2 or 4 (8 only with the lane split), a lane
+    flag other than 0 or 1 and tile shapes outside 0..2 are refused with PMSP_EINVAL
+    before anything runs; the context stays usable."""
     p = scenes.config0(W=64, H=32)
     args = _args(p)
     for bad in (pm.pmsp_tuning(0, 0, 0, 1, 0, 3), pm.pmsp_tuning(0, 0, 0, 1, 0, 8), pm.pmsp_tuning(0, 0, 0, 1, 3, 1),
-                pm.pmsp_tuning(0, 0, 0, 1, 0, 2, 2), pm.pmsp_tuning(0, 0, 0, 1, 0, 2, -1)):
+                pm.pmsp_tuning(0, 0, 0, 1, 0, 2, 2), pm.pmsp_tuning(0, 0, 0, 1, 0, 2, -1),
+                pm.pmsp_tuning(0, 0, 0, 1, 0, 16, 1)):
         with pytest.raises(pm.PmspError) as e:
             pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=bad)
         assert e.value.code == pm.PMSP_EINVAL
     pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=pm.pmsp_tuning(0, 0, 0, 1, 0, 2))
     pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=pm.pmsp_tuning(0, 0, 0, 1, 0, 4, 1))
+    pm.pmsp_densify_batch(ctx, pm.Batch([(*args, p.params, None)]), tuning=pm.pmsp_tuning(0, 0, 0, 1, 0, 8, 1))
     pm.pmsp_sync(ctx)
