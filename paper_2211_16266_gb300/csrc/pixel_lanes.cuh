@@ -25,6 +25,7 @@
 #pragma once
 
 #include "pixel_kernel.cuh"
+#include "sample_split.h"
 
 namespace pmsp {
 
@@ -83,14 +84,11 @@ __device__ __forceinline__ float plane_cost_lanes(const PixelParams& P, const SM
         if (ODD) c0o = view_sample<ParamViews>(P.src[NS - 1], X, Y, Z);
     }
     bool valid = true;
-    // this lane's first sample (a, b) = divmod(sub, K), then steps of T samples
-    int a = 0, b = sub;
-    while (b >= K) {
-        b -= K;
-        ++a;
-    }
+    // this lane's samples: m = sub, sub + T, ... in row-major order (sample_split.h)
+    int a, b;
+    split_first_sample(sub, K, a, b);
 #pragma unroll 1
-    for (; a < K;) {
+    for (; a < K; split_next_sample(T, K, a, b)) {
         if (!(a == ac && b == ac)) {
             const int oy = a * stp - R;
             const float cl = sm.row_cos[ly + oy], msl = -sm.row_sin[ly + oy];
@@ -122,11 +120,6 @@ __device__ __forceinline__ float plane_cost_lanes(const PixelParams& P, const SM
                 SJJo = fmaf(tw, Jc, SJJo);
                 SIJo = fmaf(wI, Jc, SIJo);
             }
-        }
-        b += T;
-        while (b >= K) {
-            b -= K;
-            ++a;
         }
     }
     // the group's sums and validity, identical in all T lanes
