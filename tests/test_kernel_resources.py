@@ -2,7 +2,9 @@
 
 The 6- and 8-view half-sweeps run 4 blocks of 128 threads per SM within 128
 registers a thread and without spills (measured faster than 5-7 blocks with
-spills); the thread-split kernels keep 8 blocks within 64 registers. This
+spills); the thread-split kernels keep 8 blocks within 64 registers, and the
+lane-split kernels (2, 4 or 8 lanes per pixel, every lane holding all views'
+sums) the one-thread budget, spill-free. This
 builds those translation units for sm_103a with `-Xptxas -v` and checks
 registers, spills and shared memory of every pixel kernel instance in them
 against the budget the measured configuration used.
@@ -49,7 +51,8 @@ def test_pixel_instances_stay_within_the_measured_budget(tu, tmp_path):
     rep = _report(tu, tmp_path)
     pixel = {k: v for k, v in rep.items() if "pixel_kernel" in k}
     split = {k: v for k, v in rep.items() if "pixel_split_kernel" in k}
-    assert len(pixel) >= 9 and len(split) == 4, sorted(rep)
+    lanes = {k: v for k, v in rep.items() if "pixel_lanes_kernel" in k}
+    assert len(pixel) >= 9 and len(split) == 4 and len(lanes) == 6, sorted(rep)
     for name, v in pixel.items():
         assert v["regs"] <= 128, (name, v)             # 4 blocks x 128 threads per SM
         assert v["spill"] == 0, (name, v)
@@ -57,3 +60,7 @@ def test_pixel_instances_stay_within_the_measured_budget(tu, tmp_path):
     for name, v in split.items():
         assert v["regs"] <= 64, (name, v)              # 8 blocks x 128 threads per SM
         assert v["smem"] * 8 <= 228 * 1024, (name, v)
+    for name, v in lanes.items():
+        assert v["regs"] <= 128, (name, v)             # 4 blocks x 128 threads per SM
+        assert v["spill"] == 0, (name, v)
+        assert v["smem"] * 4 <= 228 * 1024, (name, v)
